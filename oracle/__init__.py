@@ -70,6 +70,9 @@ def _load():
                                    C.c_int, i64, i32, i32, P], C.c_int),
                 "oracle_lj_adjoint": ([i64, P, P, P, i32, P, P, dbl, C.c_int, P, P, i32, P, dbl,
                                        P, P, P], None),
+                "oracle_lj_forces_sample": ([i64, P, P, P, i32, P, P, dbl, C.c_int, i64, P, P, P],
+                                            None),
+                "oracle_neighbors_sample": ([i64, P, P, dbl, i64, P, i32, P, P], C.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -286,3 +289,37 @@ def lj_adjoint(x, types, box, G, gE: float, eps=((1.0,),), sigma=((1.0,),), rc: 
                                   _p(nn), _p(nbr), nbr.shape[1], _p(G), float(gE), _p(dx), _p(de),
                                   _p(ds))
     return dx, de.reshape(nt, nt), ds.reshape(nt, nt)
+
+
+def lj_forces_sample(x, types, box, idx, eps=((1.0,),), sigma=((1.0,),), rc: float = 2.5,
+                     shift: bool = False):
+    """Forces (m,3) and per-atom energies (m,) of atoms idx, by brute force
+    over all atoms (for systems too large to list in full)."""
+    x = _f64(x)
+    L = _f64(box, (3,))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    eps_a = np.atleast_2d(np.asarray(eps, dtype=np.float64))
+    nt = eps_a.shape[0]
+    e, s = _params(nt, eps_a, sigma)
+    f = np.zeros((idx.size, 3))
+    ea = np.zeros(idx.size)
+    _load().oracle_lj_forces_sample(x.shape[0], _p(x), _p(_i32(types)), _p(L), nt, _p(e), _p(s),
+                                    float(rc), int(shift), idx.size, _p(idx), _p(f), _p(ea))
+    return f, ea
+
+
+def neighbors_sample(x, box, rs: float, idx, maxnb: int = 256):
+    """Neighbor rows (canonical r^2 < rs^2) of atoms idx by brute force:
+    list of frozensets of atom indices."""
+    x = _f64(x)
+    L = _f64(box, (3,))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    while True:
+        nn = np.zeros(idx.size, dtype=np.int32)
+        nbr = np.zeros((idx.size, maxnb), dtype=np.int32)
+        rc_ = _load().oracle_neighbors_sample(x.shape[0], _p(x), _p(L), float(rs), idx.size,
+                                              _p(idx), int(maxnb), _p(nn), _p(nbr))
+        if rc_ < 0:
+            maxnb = -rc_
+            continue
+        return [frozenset(nbr[s, : nn[s]].tolist()) for s in range(idx.size)]

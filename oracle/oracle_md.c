@@ -557,3 +557,56 @@ void oracle_lj_adjoint(int64_t n, const double *x, const int32_t *type, const do
     free(acc);
     free(pe_);
 }
+
+/* ------------------------------------------------------------------------
+ * Sampled outputs for systems too large to list in full: for each of the m
+ * atoms idx[s], its force (by brute force over all j, pairs closer than rc)
+ * and its neighbor row (all j with canonical r^2 < rs^2, increasing j).
+ * Same definitions as oracle_lj_forces_brute / oracle_neighbors_brute.
+ * ------------------------------------------------------------------------ */
+void oracle_lj_forces_sample(int64_t n, const double *x, const int32_t *type, const double L[3],
+                             int32_t ntypes, const double *eps, const double *sigma, double rc,
+                             int shift, int64_t m, const int64_t *idx, double *f, double *e_atom) {
+    const double rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t s = 0; s < m; ++s) {
+        const int64_t i = idx[s];
+        double fi[3] = {0.0, 0.0, 0.0};
+        double ei = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            min_image(&x[3 * i], &x[3 * j], L, d);
+            double u = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            if (!(u < rc2)) continue;
+            int32_t ab = type[i] * ntypes + type[j];
+            double phi, U;
+            lj_pair(u, eps[ab], sigma[ab], rc, shift, &phi, &U);
+            for (int a = 0; a < 3; ++a) fi[a] += phi * d[a];
+            ei += 0.5 * U;
+        }
+        for (int a = 0; a < 3; ++a) f[3 * s + a] = fi[a];
+        if (e_atom) e_atom[s] = ei;
+    }
+}
+
+int oracle_neighbors_sample(int64_t n, const double *x, const double L[3], double rs, int64_t m,
+                            const int64_t *idx, int32_t maxnb, int32_t *nn, int32_t *nbr) {
+    const double rs2 = rs * rs;
+    int32_t worst = 0;
+#pragma omp parallel for schedule(dynamic) reduction(max : worst)
+    for (int64_t s = 0; s < m; ++s) {
+        const int64_t i = idx[s];
+        int32_t cnt = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (canonical_r2(&x[3 * i], &x[3 * j], L) < rs2) {
+                if (cnt < maxnb) nbr[s * maxnb + cnt] = (int32_t)j;
+                cnt += 1;
+            }
+        }
+        nn[s] = cnt;
+        if (cnt > worst) worst = cnt;
+    }
+    return worst > maxnb ? -worst : ORACLE_OK;
+}

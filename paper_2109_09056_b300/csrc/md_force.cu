@@ -1,0 +1,560 @@
+// md_force.cu -- Lennard-Jones 12-6 pair forces over the Verlet list, fused
+// with the velocity-Verlet update (paper: the LJ short-range benchmark kernel
+// of CabanaMD, Section "CabanaMD"; "forces are calculated to propagate the
+// particles to new positions", Introduction).
+//
+// Per pair, with d = x_j - x_i and r^2 = |d|^2 < rc^2:
+//   phi = 24 eps / r^2 [2 (sigma^2/r^2)^6 - (sigma^2/r^2)^3],  F_i += -phi d,
+//   e_i += 1/2 * 4 eps [(sigma^2/r^2)^6 - (sigma^2/r^2)^3]  (- U(rc) if shifted).
+//
+// Mixed precision: pair arithmetic in FP32 on the cell-local shadow
+// coordinates (x_j - x_i = (s_j + delta h) - s_i, delta from the list entry's
+// stencil code); each lane keeps Kahan-compensated FP32 sums of its share of
+// the neighbors; the T lanes of an atom merge their (sum, compensation) pairs
+// with TwoSum in a fixed xor-shuffle tree; the result is converted to FP64
+// once.  Velocities, positions and energy totals are FP64.
+//
+// Launch: persistent grid (SM count x resident CTAs); warp w of the grid takes
+// warp-tiles w, w + nwarps, ...; a warp-tile is A = 32/T consecutive atoms,
+// T lanes each.  The list row for step q of a warp-tile is one 128-byte load.
+//
+// Modes: FORCE_ONLY (store F, energy), FINAL (store F, v += dt/2 F/m, thermo),
+// FUSED (v += dt/2 F/m [thermo at v_n] v += dt/2 F/m, x += dt v, write the next
+// shadow; the list-side reads use the current buffers, writes go to the
+// other buffer, so the kernel never reads what it writes).
+#include "md_common.cuh"
+
+namespace mdb {
+namespace {
+
+constexpr int kMaxWarps = 16;
+
+struct ForceArgs {
+    const Box *boxes;
+    const int32_t *tile_box;
+    const Pair *pair;
+    int64_t ns, nwt;  // slots, warp-tiles
+    int pad, R;
+    const float4 *sh_in;
+    float4 *sh_out;
+    const double *r_in;
+    double *r_out;
+    double *v;
+    double *f;
+    const double *rbuild;
+    const int32_t *type;
+    const int32_t *nn;
+    const uint32_t *nbr;
+    double *tpart;
+    Flags *fl;
+    int mode;
+    int thermo_every;
+    unsigned int *done;
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float t) {
+    const float y = t - c;
+    const float u = s + y;
+    c = (u - s) - y;
+    s = u;
+}
+
+// Merge (s, c) pairs (value = s - c) of the T lanes of an atom with TwoSum.
+template <int T>
+__device__ __forceinline__ void merge_lanes(float &s, float &c) {
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        const float S = s + s2;
+        const float bp = S - s;
+        const float err = (s - (S - bp)) + (s2 - bp);
+        c = (c + c2) - err;
+        s = S;
+    }
+}
+
+template <int T>
+__device__ __forceinline__ double sum_lanes_d(double x) {
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_max_d(double x) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Shared per-CTA tables.
+struct SmemTabs {
+    float fe24[64], fs2[64], fe4[64], fush[64];
+    double de24[64], ds2[64], de4[64], dush[64];
+    double dtm[MD_MAXT], hdtm[MD_MAXT], mass[MD_MAXT];
+};
+
+// The velocity-Verlet epilogue for component d of atom i; returns the new
+// shadow coordinate (FUSED) and accumulates thermo terms.
+template <bool THERMO>
+__device__ __forceinline__ float epilogue(const ForceArgs &a, const SmemTabs &tb, int64_t i, int d,
+                                          int ti, double F, double &ke, double &p, double &disp2) {
+    const int64_t o = d * a.ns + i;
+    float snew = 0.f;
+    if (a.mode == MODE_FORCE_ONLY) {
+        a.f[o] = F;
+        if (THERMO) {
+            const double vv = a.v[o];
+            ke += 0.5 * tb.mass[ti] * vv * vv;
+            p += tb.mass[ti] * vv;
+            const double dd = a.r_in[o] - a.rbuild[o];
+            disp2 += dd * dd;
+        }
+    } else if (a.mode == MODE_FINAL) {
+        a.f[o] = F;
+        const double vv = fma(tb.hdtm[ti], F, a.v[o]);
+        a.v[o] = vv;
+        if (THERMO) {
+            ke += 0.5 * tb.mass[ti] * vv * vv;
+            p += tb.mass[ti] * vv;
+            const double dd = a.r_in[o] - a.rbuild[o];
+            disp2 += dd * dd;
+        }
+    } else {
+        double vv;
+        if (THERMO) {
+            const double vh = fma(tb.hdtm[ti], F, a.v[o]);
+            ke += 0.5 * tb.mass[ti] * vh * vh;
+            p += tb.mass[ti] * vh;
+            const double dd = a.r_in[o] - a.rbuild[o];
+            disp2 += dd * dd;
+            vv = fma(tb.hdtm[ti], F, vh);
+        } else {
+            vv = fma(tb.dtm[ti], F, a.v[o]);
+        }
+        a.v[o] = vv;
+        const double rn = fma(a.pair->dt, vv, a.r_in[o]);
+        a.r_out[o] = rn;
+        snew = __double2float_rn(rn);
+    }
+    return snew;
+}
+
+template <bool MIXED, int T, bool ONE, bool THERMO>
+__device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &tb,
+                                           float4 (*s_offf)[27], double (*s_offd)[81]) {
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int sub = lane % T;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int nt = a.pair->nt;
+    const float rc2f = a.pair->rc2f;
+    const double rc2 = a.pair->rc2;
+    const float e24_0 = tb.fe24[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
+    const double de24_0 = tb.de24[0], ds2_0 = tb.ds2[0], de4_0 = tb.de4[0], dush_0 = tb.dush[0];
+    int curbox = -1;
+    for (int64_t wt = gw; wt < a.nwt; wt += nw) {
+        const int64_t i = wt * A + lane / T;
+        const int b = a.tile_box[(wt * A) >> 5];
+        const Box &B = a.boxes[b];
+        if (b != curbox) {
+            if (lane < 27) {
+                const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+                if (MIXED) {
+                    s_offf[wib][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
+                                                    (float)oz * B.hf[2], 0.f);
+                } else {
+                    s_offd[wib][3 * lane + 0] = (double)ox * B.h[0];
+                    s_offd[wib][3 * lane + 1] = (double)oy * B.h[1];
+                    s_offd[wib][3 * lane + 2] = (double)oz * B.h[2];
+                }
+            }
+            __syncwarp();
+            curbox = b;
+        }
+        const bool valid = (i - B.slot_off) < B.n;
+        const int ni = valid ? min(a.nn[i], a.pad) : 0;
+        const uint32_t *row = a.nbr + (size_t)wt * a.R * 32 + lane;
+        double Fd[3];
+        double ped = 0.0;
+        int ti;
+        if (MIXED) {
+            const float4 si = a.sh_in[i];
+            ti = ONE ? 0 : __float_as_int(si.w);
+            float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
+            int q = 0;
+            for (int k = sub; k < ni; k += T, ++q) {
+                const uint32_t e = __ldcs(row + (size_t)q * 32);
+                const uint32_t j = e & MD_IDX_MASK;
+                const float4 sj = __ldg(a.sh_in + j);
+                const float4 o = s_offf[wib][e >> MD_IDX_BITS];
+                const float dx = (sj.x + o.x) - si.x;
+                const float dy = (sj.y + o.y) - si.y;
+                const float dz = (sj.z + o.z) - si.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < rc2f) {
+                    float e24, s2, e4, ush;
+                    if (ONE) {
+                        e24 = e24_0; s2 = s2_0; e4 = e4_0; ush = ush_0;
+                    } else {
+                        const int ab = ti * nt + __float_as_int(sj.w);
+                        e24 = tb.fe24[ab]; s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
+                    }
+                    const float r2inv = __fdividef(1.0f, r2);
+                    const float q2 = s2 * r2inv;
+                    const float s6 = q2 * q2 * q2;
+                    const float phi = e24 * r2inv * s6 * fmaf(2.0f, s6, -1.0f);
+                    kahan_add(fx, cx, -phi * dx);
+                    kahan_add(fy, cy, -phi * dy);
+                    kahan_add(fz, cz, -phi * dz);
+                    if (THERMO) kahan_add(pe, cp, 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush));
+                }
+            }
+            merge_lanes<T>(fx, cx);
+            merge_lanes<T>(fy, cy);
+            merge_lanes<T>(fz, cz);
+            Fd[0] = (double)fx; Fd[1] = (double)fy; Fd[2] = (double)fz;
+            if (THERMO) {
+                merge_lanes<T>(pe, cp);
+                ped = (double)pe;
+            }
+        } else {
+            const double rix = a.r_in[i], riy = a.r_in[a.ns + i], riz = a.r_in[2 * a.ns + i];
+            ti = ONE ? 0 : a.type[i];
+            double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
+            int q = 0;
+            for (int k = sub; k < ni; k += T, ++q) {
+                const uint32_t e = __ldcs(row + (size_t)q * 32);
+                const uint32_t j = e & MD_IDX_MASK;
+                const double *o = s_offd[wib] + 3 * (e >> MD_IDX_BITS);
+                const double dx = (__ldg(a.r_in + j) + o[0]) - rix;
+                const double dy = (__ldg(a.r_in + a.ns + j) + o[1]) - riy;
+                const double dz = (__ldg(a.r_in + 2 * a.ns + j) + o[2]) - riz;
+                const double r2 = (dx * dx + dy * dy) + dz * dz;
+                if (r2 < rc2) {
+                    double e24, s2, e4, ush;
+                    if (ONE) {
+                        e24 = de24_0; s2 = ds2_0; e4 = de4_0; ush = dush_0;
+                    } else {
+                        const int ab = ti * nt + __ldg(a.type + j);
+                        e24 = tb.de24[ab]; s2 = tb.ds2[ab]; e4 = tb.de4[ab]; ush = tb.dush[ab];
+                    }
+                    const double r2inv = 1.0 / r2;
+                    const double q2 = s2 * r2inv;
+                    const double s6 = q2 * q2 * q2;
+                    const double phi = e24 * r2inv * s6 * (2.0 * s6 - 1.0);
+                    fx -= phi * dx;
+                    fy -= phi * dy;
+                    fz -= phi * dz;
+                    if (THERMO) pe += 0.5 * (e4 * s6 * (s6 - 1.0) - ush);
+                }
+            }
+            Fd[0] = sum_lanes_d<T>(fx);
+            Fd[1] = sum_lanes_d<T>(fy);
+            Fd[2] = sum_lanes_d<T>(fz);
+            if (THERMO) ped = sum_lanes_d<T>(pe);
+        }
+        // Epilogue: lane `sub` handles components sub, sub + T, ...
+        double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
+        float snew[3] = {0.f, 0.f, 0.f};
+        if (valid) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d % T == sub) {
+                    double pp = 0.0;
+                    snew[d] = epilogue<THERMO>(a, tb, i, d, ti, Fd[d], ke, pp, disp2);
+                    pd[d] = pp;
+                }
+            }
+        }
+        if (a.mode == MODE_FUSED) {
+            float s3[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                s3[d] = __shfl_sync(0xffffffffu, snew[d], (lane - sub) + d % T);
+            if (valid && sub == 0) a.sh_out[i] = make_float4(s3[0], s3[1], s3[2], __int_as_float(ti));
+        }
+        if (THERMO) {
+            // displacement^2 of the atom = sum over its components (spread over lanes)
+            const double dsum = sum_lanes_d<T>(disp2);
+            const double pe_t = warp_sum_d((valid && sub == 0) ? ped : 0.0);
+            const double ke_t = warp_sum_d(ke);
+            const double px = warp_sum_d(pd[0]), py = warp_sum_d(pd[1]), pz = warp_sum_d(pd[2]);
+            const double dm = warp_max_d(valid ? dsum : 0.0);
+            if (lane == 0) {
+                double *tp = a.tpart + wt * TP;
+                tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
+            }
+        }
+    }
+}
+
+template <bool MIXED, int T, bool ONE>
+__global__ void __launch_bounds__(256) k_force(ForceArgs a) {
+    if (a.fl->status & ST_FREEZE) {
+        // Frozen (a list overflowed earlier in this run): keep the state and
+        // mirror it into the output buffers so the buffer flip stays valid.
+        if (a.mode == MODE_FUSED) {
+            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
+                 t += (int64_t)gridDim.x * blockDim.x) {
+                a.sh_out[t] = a.sh_in[t];
+                for (int d = 0; d < 3; ++d) a.r_out[d * a.ns + t] = a.r_in[d * a.ns + t];
+            }
+        }
+        return;
+    }
+    __shared__ SmemTabs tb;
+    __shared__ __align__(16) float4 s_offf[MIXED ? kMaxWarps : 1][27];
+    __shared__ __align__(16) double s_offd[MIXED ? 1 : kMaxWarps][81];
+    const Pair &P = *a.pair;
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+        tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
+        tb.de24[t] = P.e24[t]; tb.ds2[t] = P.s2[t]; tb.de4[t] = P.e4[t]; tb.dush[t] = P.ush[t];
+        if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
+    }
+    __syncthreads();
+    const int64_t clock = a.fl->clock;
+    const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
+    if (thermo) force_body<MIXED, T, ONE, true>(a, tb, s_offf, s_offd);
+    else force_body<MIXED, T, ONE, false>(a, tb, s_offf, s_offd);
+    // The last CTA to finish records which step the thermo partials describe
+    // and, in FUSED mode, advances the step clock (every CTA has read it).
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(a.done, 1u);
+        if (prev == gridDim.x - 1) {
+            *a.done = 0u;
+            a.fl->thermo = thermo ? 1u : 0u;
+            if (a.mode == MODE_FUSED) a.fl->clock = clock + 1;
+        }
+    }
+}
+
+// v += dt/2 F/m; x += dt v; shadow refresh.  From a READY state.
+__global__ void k_kick_drift(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                             const Pair *__restrict__ pair, int64_t ns,
+                             const int32_t *__restrict__ type, const double *__restrict__ f,
+                             double *__restrict__ v, const double *__restrict__ r_in,
+                             double *__restrict__ r_out, float4 *__restrict__ sh_out, Flags *fl) {
+    if (fl->status & ST_FREEZE) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) fl->clock += 1;
+    if (i >= ns) return;
+    const Box &B = boxes[tile_box[i >> 5]];
+    const int ty = type[i];
+    float s[3] = {0.f, 0.f, 0.f};
+    if (i - B.slot_off < B.n) {
+        const double hdtm = pair->hdtm[ty], dt = pair->dt;
+        for (int d = 0; d < 3; ++d) {
+            const int64_t o = d * ns + i;
+            const double vv = fma(hdtm, f[o], v[o]);
+            v[o] = vv;
+            const double rn = fma(dt, vv, r_in[o]);
+            r_out[o] = rn;
+            s[d] = __double2float_rn(rn);
+        }
+    } else {
+        for (int d = 0; d < 3; ++d) r_out[d * ns + i] = 0.0;
+    }
+    sh_out[i] = make_float4(s[0], s[1], s[2], __int_as_float(ty));
+}
+
+// One CTA per box: fixed-order reduction of the warp-tile partials.
+__global__ void __launch_bounds__(256) k_finalize(const Box *__restrict__ boxes, int A,
+                                                  const double *__restrict__ tpart,
+                                                  double *__restrict__ tbox, Flags *fl,
+                                                  double *__restrict__ tlog, int32_t tlog_cap,
+                                                  int thermo_every, int mode) {
+    if (fl->status & ST_FREEZE) return;
+    if (fl->thermo == 0u) return;  // the force kernel computed no thermo this step
+    const int b = blockIdx.x;
+    const Box &B = boxes[b];
+    const int64_t w0 = B.slot_off / A, w1 = (B.slot_off + B.npad) / A;
+    __shared__ double red[6][256];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        const double *tp = tpart + w * TP;
+        for (int q = 0; q < 5; ++q) acc[q] += tp[q];
+        acc[5] = fmax(acc[5], tp[5]);
+    }
+    for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int s = 128; s >= 1; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+            red[5][threadIdx.x] = fmax(red[5][threadIdx.x], red[5][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // step the numbers describe: FUSED already advanced the clock
+        const int64_t step = fl->clock - (mode == MODE_FUSED ? 1 : 0);
+        double *tb = tbox + b * TB;
+        for (int q = 0; q < 5; ++q) tb[q] = red[q][0];
+        tb[5] = sqrt(red[5][0]);
+        tb[6] = (double)step;
+        if (b == 0 && thermo_every > 0 && step % thermo_every == 0) {
+            const int64_t row = step / thermo_every;
+            if (row < tlog_cap) {
+                tlog[4 * row + 0] = (double)step;
+                tlog[4 * row + 1] = red[0][0];
+                tlog[4 * row + 2] = red[1][0];
+                tlog[4 * row + 3] = red[0][0] + red[1][0];
+            }
+        }
+    }
+}
+
+__global__ void k_get_state(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                            int64_t ns, const double *__restrict__ r,
+                            const int32_t *__restrict__ cellc, const double *__restrict__ v,
+                            const double *__restrict__ f, const int32_t *__restrict__ img,
+                            const int32_t *__restrict__ id, double *__restrict__ xo,
+                            double *__restrict__ vo, double *__restrict__ fo,
+                            int32_t *__restrict__ imgo, int32_t *__restrict__ ido,
+                            const int32_t *__restrict__ ty, int32_t *__restrict__ tyo) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    const Box &B = boxes[tile_box[k >> 5]];
+    const int64_t loc = k - B.slot_off;
+    if (loc >= B.n) return;
+    const int64_t g = id[k];
+    int cc[3];
+    unpack_cell(cellc[k], cc[0], cc[1], cc[2]);
+    for (int d = 0; d < 3; ++d) {
+        if (xo) xo[3 * g + d] = __dadd_rn(cell_centre(cc[d], B.h[d]), r[d * ns + k]);
+        if (vo) vo[3 * g + d] = v[d * ns + k];
+        if (fo) fo[3 * g + d] = f[d * ns + k];
+        if (imgo) imgo[3 * g + d] = img[d * ns + k];
+    }
+    if (ido) ido[B.atom_base + loc] = (int32_t)g;
+    if (tyo) tyo[g] = ty[k];
+}
+
+__global__ void k_get_neighbors(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                                int64_t ns, int T, int R, int pad, const int32_t *__restrict__ nn,
+                                const uint32_t *__restrict__ nbr, int pad_out,
+                                int32_t *__restrict__ nn_out, int32_t *__restrict__ nbr_out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const Box &B = boxes[tile_box[i >> 5]];
+    const int64_t loc = i - B.slot_off;
+    if (loc >= B.n) return;
+    const int64_t u = B.atom_base + loc;
+    const int cnt = nn[i];
+    if (nn_out) nn_out[u] = cnt;
+    if (!nbr_out) return;
+    const int A = 32 / T;
+    const int m = min(cnt, min(pad, pad_out));
+    for (int k = 0; k < m; ++k) {
+        const uint32_t e = nbr[((size_t)(i / A) * R + k / T) * 32 + (i % A) * T + k % T];
+        const int64_t j = e & MD_IDX_MASK;
+        nbr_out[u * pad_out + k] = (int32_t)(B.atom_base + (j - B.slot_off));
+    }
+}
+
+template <bool MIXED, int T, bool ONE>
+cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
+    static int grid_cache[2][9][2][9] = {};
+    int &g = grid_cache[MIXED][T][ONE][(c->block / 32) & 7];
+    if (g == 0) {
+        int per = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force<MIXED, T, ONE>,
+                                                                       c->block, 0);
+        if (e != cudaSuccess) return e;
+        g = per > 0 ? per : 1;
+    }
+    const int64_t warps_per_block = c->block / 32;
+    int64_t grid = (int64_t)c->nsm * g;
+    const int64_t need = (a.nwt + warps_per_block - 1) / warps_per_block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k_force<MIXED, T, ONE><<<(unsigned)grid, c->block, 0, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool MIXED>
+cudaError_t launch_force_m(md_ctx *c, const ForceArgs &a) {
+    const bool one = c->hpair.nt == 1;
+    switch (c->T) {
+        case 1: return one ? launch_force_t<MIXED, 1, true>(c, a) : launch_force_t<MIXED, 1, false>(c, a);
+        case 2: return one ? launch_force_t<MIXED, 2, true>(c, a) : launch_force_t<MIXED, 2, false>(c, a);
+        case 4: return one ? launch_force_t<MIXED, 4, true>(c, a) : launch_force_t<MIXED, 4, false>(c, a);
+        case 8: return one ? launch_force_t<MIXED, 8, true>(c, a) : launch_force_t<MIXED, 8, false>(c, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_force(md_ctx *c, int mode) {
+    ForceArgs a;
+    a.boxes = c->dbox;
+    a.tile_box = c->tile_box;
+    a.pair = c->dpair;
+    a.ns = c->ns;
+    a.nwt = c->ns / (32 / c->T);
+    a.pad = c->pad;
+    a.R = c->R;
+    a.sh_in = c->sh[c->pc];
+    a.sh_out = c->sh[c->pc ^ 1];
+    a.r_in = c->r[c->pc];
+    a.r_out = c->r[c->pc ^ 1];
+    a.v = c->v[c->oc];
+    a.f = c->f;
+    a.rbuild = c->rbuild;
+    a.type = c->type[c->oc];
+    a.nn = c->nn;
+    a.nbr = c->nbr;
+    a.tpart = c->tpart;
+    a.fl = c->dflags;
+    a.mode = mode;
+    a.thermo_every = c->params.thermo_every;
+    a.done = &c->dflags->done;
+    cudaError_t e = c->params.precision == MD_MIXED ? launch_force_m<true>(c, a)
+                                                    : launch_force_m<false>(c, a);
+    if (e == cudaSuccess && mode == MODE_FUSED) c->pc ^= 1;
+    return e;
+}
+
+cudaError_t launch_kick_drift(md_ctx *c) {
+    const int t = 256;
+    k_kick_drift<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
+        c->dbox, c->tile_box, c->dpair, c->ns, c->type[c->oc], c->f, c->v[c->oc], c->r[c->pc],
+        c->r[c->pc ^ 1], c->sh[c->pc ^ 1], c->dflags);
+    c->pc ^= 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(md_ctx *c, int mode) {
+    k_finalize<<<c->nbox, 256, 0, c->stream>>>(c->dbox, 32 / c->T, c->tpart, c->tbox, c->dflags,
+                                                c->tlog, c->tlog_cap, c->params.thermo_every, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(md_ctx *c, double *x_aos, double *v_aos, double *f_aos,
+                             int32_t *img_aos, int32_t *ids, int32_t *types) {
+    const int t = 256;
+    k_get_state<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
+        c->dbox, c->tile_box, c->ns, c->r[c->pc], c->cellc[c->oc], c->v[c->oc], c->f,
+        c->img[c->oc], c->id[c->oc], x_aos, v_aos, f_aos, img_aos, ids, c->type[c->oc], types);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_neighbors(md_ctx *c, int32_t *nn_out, int32_t *nbr_out, int pad_out) {
+    const int t = 256;
+    k_get_neighbors<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
+        c->dbox, c->tile_box, c->ns, c->T, c->R, c->pad, c->nn, c->nbr, pad_out, nn_out, nbr_out);
+    return cudaGetLastError();
+}
+
+}  // namespace mdb

@@ -1,0 +1,288 @@
+// md_sort.cu -- the resort step: wrap, geometric binning, stable cell-order
+// permutation and the gather of all per-atom state into the new order
+// (paper, Section "Particle Sorting": sorting by geometric binning; the
+// Introduction's timestep ends with "the particles are then resorted").
+//
+//   k_bin      : x = O + r (or raw input), wrap into [0, L), cell id, atomic
+//                histogram; each atom takes a slot rank inside its cell.
+//   k_scan     : exclusive prefix sum of the per-cell counts (one CTA), plus the
+//                per-build bookkeeping (dangerous-build test, counter resets).
+//   k_scatter  : atom -> slot (cell start + atomic rank).
+//   k_segsort  : per cell, order the slots by prior index, which makes the
+//                permutation stable: new order = sort by (cell, prior index).
+//   k_permute  : gather r, v, type, id, image counts into the new order, with
+//                r re-expressed relative to the new cell's centre and the FP32
+//                shadow refreshed.
+//
+// Every FP64 operation that decides a cell or a wrapped coordinate is an
+// explicitly rounded intrinsic (no FMA contraction), so the wrapped positions
+// and cell ids are bit-identical to the textbook definition.
+#include "md_common.cuh"
+
+namespace mdb {
+namespace {
+
+__global__ void k_unpack(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                         int64_t ns, const double *__restrict__ x, const double *__restrict__ v,
+                         const int32_t *__restrict__ types, double *__restrict__ xraw,
+                         double *__restrict__ vout, int32_t *__restrict__ tout,
+                         int32_t *__restrict__ idout, int32_t *__restrict__ imgout,
+                         int32_t *__restrict__ cellc) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const Box &B = boxes[tile_box[i >> 5]];
+    int64_t loc = i - B.slot_off;
+    if (loc < B.n) {
+        int64_t g = B.atom_base + loc;
+        for (int d = 0; d < 3; ++d) {
+            if (x) xraw[d * ns + i] = x[3 * g + d];
+            vout[d * ns + i] = v ? v[3 * g + d] : 0.0;
+            imgout[d * ns + i] = 0;
+        }
+        tout[i] = types ? types[g] : 0;
+        idout[i] = (int32_t)g;
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            if (x) xraw[d * ns + i] = 0.0;
+            vout[d * ns + i] = 0.0;
+            imgout[d * ns + i] = 0;
+        }
+        tout[i] = 0;
+        idout[i] = -1;
+    }
+    cellc[i] = 0;
+}
+
+__global__ void k_bin(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                      int64_t ns, int raw, const double *__restrict__ r,
+                      const double *__restrict__ xraw, const int32_t *__restrict__ cellc,
+                      int32_t *__restrict__ img, const double *__restrict__ rbuild,
+                      double *__restrict__ xw, int32_t *__restrict__ cell,
+                      int32_t *__restrict__ rank, int32_t *__restrict__ count, Flags *fl) {
+    if (fl->status & ST_FREEZE) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const Box &B = boxes[tile_box[i >> 5]];
+    if (i - B.slot_off >= B.n) return;
+    double x[3];
+    float disp2 = 0.f;
+    if (raw) {
+        for (int d = 0; d < 3; ++d) x[d] = xraw[d * ns + i];
+    } else {
+        int cc[3];
+        unpack_cell(cellc[i], cc[0], cc[1], cc[2]);
+        for (int d = 0; d < 3; ++d) {
+            double rd = r[d * ns + i];
+            x[d] = __dadd_rn(cell_centre(cc[d], B.h[d]), rd);
+            float dd = (float)(rd - rbuild[d * ns + i]);
+            disp2 += dd * dd;
+        }
+    }
+    bool finite = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+    if (!finite) {
+        atomicOr(&fl->status, ST_NONFINITE);
+        return;
+    }
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        const double L = B.L[d];
+        double q = floor(__ddiv_rn(x[d], L));
+        double p = __dmul_rn(L, q);
+        double w = __dsub_rn(x[d], p);
+        int k = (int)q;
+        if (w < 0.0) { w = __dadd_rn(w, L); k -= 1; }
+        if (w >= L) { w = __dsub_rn(w, L); k += 1; }
+        img[d * ns + i] += k;
+        xw[d * ns + i] = w;
+        int cd = __double2int_rz(__dmul_rn(w, B.inv[d]));
+        cd = cd < 0 ? 0 : (cd > B.nc[d] - 1 ? B.nc[d] - 1 : cd);
+        c[d] = cd;
+    }
+    int32_t gc = B.cell_off + (c[2] * B.nc[1] + c[1]) * B.nc[0] + c[0];
+    cell[i] = gc;
+    rank[i] = atomicAdd(&count[gc], 1);
+    if (!raw) atomicMax(&fl->maxdisp_bits, __float_as_uint(sqrtf(disp2)));
+}
+
+// One CTA of 1024 threads: exclusive scan of count[0..nc) into cstart[0..nc],
+// zeroing count for the next build.
+__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ count,
+                                               int32_t *__restrict__ cstart, int32_t ncell,
+                                               Flags *fl, double half_skin, int raw) {
+    if (fl->status & ST_FREEZE) return;
+    __shared__ int32_t wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int per = (ncell + 1023) / 1024;
+    const int lo = min(ncell, tid * per), hi = min(ncell, lo + per);
+    int32_t s = 0;
+    for (int c = lo; c < hi; ++c) s += count[c];
+    // block exclusive scan of s
+    int32_t incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int32_t ws = wsum[lane];
+        int32_t wi = ws;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        wsum[lane] = wi - ws;
+    }
+    __syncthreads();
+    int32_t run = wsum[w] + incl - s;
+    for (int c = lo; c < hi; ++c) {
+        int32_t k = count[c];
+        cstart[c] = run;
+        run += k;
+        count[c] = 0;
+    }
+    if (tid == 1023) cstart[ncell] = wsum[31] + incl;
+    if (tid == 0) {
+        if (!raw && __uint_as_float(fl->maxdisp_bits) > (float)half_skin) fl->dangerous += 1;
+        fl->builds += 1;
+        fl->maxdisp_bits = 0u;
+        fl->maxnn = 0;
+        fl->sumnn = 0ull;
+    }
+}
+
+__global__ void k_scatter(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                          int64_t ns, const int32_t *__restrict__ cell,
+                          const int32_t *__restrict__ rank, const int32_t *__restrict__ cstart,
+                          int32_t *__restrict__ ptmp, const Flags *fl) {
+    if (fl->status & ST_FREEZE) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const Box &B = boxes[tile_box[i >> 5]];
+    if (i - B.slot_off >= B.n) return;
+    int32_t c = cell[i];
+    int64_t slot = B.slot_off + ((int64_t)cstart[c] - B.atom_base) + rank[i];
+    ptmp[slot] = (int32_t)i;
+}
+
+// One warp per cell: rank each slot's prior index among the cell's slots.
+__global__ void k_segsort(const Box *__restrict__ boxes, const int32_t *__restrict__ cell_box,
+                          int32_t ncell, const int32_t *__restrict__ cstart,
+                          const int32_t *__restrict__ ptmp, int32_t *__restrict__ perm,
+                          const Flags *fl) {
+    if (fl->status & ST_FREEZE) return;
+    int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wg >= ncell) return;
+    const int32_t c = (int32_t)wg;
+    const Box &B = boxes[cell_box[c]];
+    const int32_t m = cstart[c + 1] - cstart[c];
+    const int64_t s0 = B.slot_off + ((int64_t)cstart[c] - B.atom_base);
+    for (int e = lane; e < m; e += 32) {
+        int32_t val = ptmp[s0 + e];
+        int32_t rk = 0;
+        for (int u = 0; u < m; ++u) rk += (ptmp[s0 + u] < val);
+        perm[s0 + rk] = val;
+    }
+}
+
+__global__ void k_permute(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                          int64_t ns, const int32_t *__restrict__ perm,
+                          const int32_t *__restrict__ cell, const double *__restrict__ xw,
+                          const double *__restrict__ v_in, const int32_t *__restrict__ t_in,
+                          const int32_t *__restrict__ id_in, const int32_t *__restrict__ img_in,
+                          double *__restrict__ r_out, double *__restrict__ v_out,
+                          int32_t *__restrict__ t_out, int32_t *__restrict__ id_out,
+                          int32_t *__restrict__ img_out, int32_t *__restrict__ cellc_out,
+                          const int32_t *__restrict__ cellc_in,
+                          float4 *__restrict__ sh_out, double *__restrict__ rbuild,
+                          double *__restrict__ xws, int32_t *__restrict__ nn, const Flags *fl) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    if (fl->status & ST_FREEZE) {
+        // Frozen: keep the order; mirror the order-buffered arrays so the
+        // buffer flip that follows every re-sort stays valid.
+        for (int d = 0; d < 3; ++d) {
+            v_out[d * ns + k] = v_in[d * ns + k];
+            img_out[d * ns + k] = img_in[d * ns + k];
+        }
+        t_out[k] = t_in[k];
+        id_out[k] = id_in[k];
+        cellc_out[k] = cellc_in[k];
+        return;
+    }
+    const Box &B = boxes[tile_box[k >> 5]];
+    if (k - B.slot_off >= B.n) {
+        for (int d = 0; d < 3; ++d) {
+            r_out[d * ns + k] = 0.0;
+            v_out[d * ns + k] = 0.0;
+            img_out[d * ns + k] = 0;
+            rbuild[d * ns + k] = 0.0;
+            xws[d * ns + k] = 0.0;
+        }
+        t_out[k] = 0;
+        id_out[k] = -1;
+        cellc_out[k] = 0;
+        sh_out[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        nn[k] = 0;
+        return;
+    }
+    const int32_t old = perm[k];
+    const int32_t loc = cell[old] - B.cell_off;
+    const int cx = loc % B.nc[0], cy = (loc / B.nc[0]) % B.nc[1], cz = loc / (B.nc[0] * B.nc[1]);
+    const int cc[3] = {cx, cy, cz};
+    float s[3];
+    for (int d = 0; d < 3; ++d) {
+        double w = xw[d * ns + old];
+        double rd = __dsub_rn(w, cell_centre(cc[d], B.h[d]));
+        r_out[d * ns + k] = rd;
+        rbuild[d * ns + k] = rd;
+        xws[d * ns + k] = w;
+        s[d] = __double2float_rn(rd);
+        v_out[d * ns + k] = v_in[d * ns + old];
+        img_out[d * ns + k] = img_in[d * ns + old];
+    }
+    const int32_t ty = t_in[old];
+    t_out[k] = ty;
+    id_out[k] = id_in[old];
+    cellc_out[k] = pack_cell(cx, cy, cz);
+    sh_out[k] = make_float4(s[0], s[1], s[2], __int_as_float(ty));
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_unpack_input(md_ctx *c, const double *x_aos, const double *v_aos,
+                                const int32_t *types) {
+    const int t = 256;
+    k_unpack<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
+        c->dbox, c->tile_box, c->ns, x_aos, v_aos, types, c->xraw, c->v[c->oc], c->type[c->oc],
+        c->id[c->oc], c->img[c->oc], c->cellc[c->oc]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_sort(md_ctx *c, bool raw_input) {
+    const int t = 256;
+    const int oc = c->oc, pc = c->pc;
+    cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(int32_t) * (size_t)c->ncell_tot, c->stream);
+    if (e != cudaSuccess) return e;
+    k_bin<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
+        c->dbox, c->tile_box, c->ns, raw_input ? 1 : 0, c->r[pc], c->xraw, c->cellc[oc],
+        c->img[oc], c->rbuild, c->xw, c->cell, c->rank, c->count, c->dflags);
+    k_scan<<<1, 1024, 0, c->stream>>>(c->count, c->cstart, c->ncell_tot, c->dflags,
+                                       c->hpair.half_skin, raw_input ? 1 : 0);
+    k_scatter<<<blocks_for(c->ns, t), t, 0, c->stream>>>(c->dbox, c->tile_box, c->ns, c->cell,
+                                                          c->rank, c->cstart, c->ptmp,
+                                                          c->dflags);
+    k_segsort<<<blocks_for((int64_t)c->ncell_tot * 32, t), t, 0, c->stream>>>(
+        c->dbox, c->cell_box, c->ncell_tot, c->cstart, c->ptmp, c->perm, c->dflags);
+    k_permute<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
+        c->dbox, c->tile_box, c->ns, c->perm, c->cell, c->xw, c->v[oc], c->type[oc], c->id[oc],
+        c->img[oc], c->r[pc], c->v[oc ^ 1], c->type[oc ^ 1], c->id[oc ^ 1], c->img[oc ^ 1],
+        c->cellc[oc ^ 1], c->cellc[oc], c->sh[pc], c->rbuild, c->xws, c->nn, c->dflags);
+    c->oc ^= 1;
+    return cudaGetLastError();
+}
+
+}  // namespace mdb

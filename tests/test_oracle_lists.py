@@ -127,3 +127,15 @@ def test_fcc_coordination_counts(orc):
     assert np.all(nn == 78)
     nn, nbr = orc.neighbors(s.x, s.box, 2.5)
     assert np.all(nn == 54)
+
+
+def test_sampled_rows_and_forces_equal_full_versions(orc):
+    s = mi.lj_melt(6, seed=16, jitter=0.1)
+    xw, _ = orc.wrap(s.x, s.box)
+    idx = np.array([0, 5, 17, 300, 863])
+    nn, nbr = orc.neighbors(xw, s.box, 2.8)
+    full = orc.neighbor_sets(nn, nbr)
+    assert orc.neighbors_sample(xw, s.box, 2.8, idx) == [full[i] for i in idx]
+    f, ea, _ = orc.lj_forces(xw, s.types, s.box, brute=True)
+    fs, es = orc.lj_forces_sample(xw, s.types, s.box, idx)
+    assert np.array_equal(fs, f[idx]) and np.array_equal(es, ea[idx])
