@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the short-range LJ MD timestep on B300.
+
+One bench "step" = one rebuild period: 20 MD timesteps of the whole hot path
+(wrap + bin + stable re-sort + Verlet-list build once, then 20 x LJ forces
+with the fused velocity-Verlet update).  Default workload: the 4,000,000-atom
+FCC 100^3 LJ melt (rho* 0.8442, +-0.05 sigma jitter, T* 1.44, rc 2.5, skin 0.3,
+dt 0.005, rebuild every 20), mixed precision.  Synthetic, seeded inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is device-timed (inputs resident in HBM, CUDA
+events on the library's stream); `e2e` goes through the C ABI with pinned HOST
+buffers (state uploaded and read back every step); `roofline` is for the
+dominant kernel (the mixed force kernel) timed live with per-launch CUDA
+events; `cpu_baseline` is the FP64 oracle on the host cores (bounded sample).
+The reference arm (`--impl reference`) times the oracle itself.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s LJ 4M atoms, mixed vs FP64 on 1 B300; pair-force % of roofline"
+UNIT = "atom-steps/s"
+MD_PER_STEP = 20
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lj_fcc100_4m")
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class Dist:
+    """Replicas: one independent system per rank; only timing is collective."""
+
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if self.pg is None:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = [[f.strip() for f in r.split(",")] for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for r in rows for k, nm in enumerate(names) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_record(kernel_file: str):
+    """DRAM bytes per launch of the force kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "force_kernel_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
+    return rec if rec.get("kernel_sha256") == sha else None
+
+
+def oracle_sample(sysd):
+    """Oracle on the full workload: the entry re-sort + list build + forces
+    (t0) and the same plus 2 steps (t2); a 20-step period is scaled as
+    t0 + 19 * (t2 - t0) / 2.  Returns (atom-steps/s, CPU seconds, threads, period s)."""
+    import oracle
+    t = time.perf_counter()
+    oracle.md_run(sysd.x, sysd.v, sysd.types, sysd.box, 0)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.md_run(sysd.x, sysd.v, sysd.types, sysd.box, 2)
+    t2 = time.perf_counter() - t
+    period = t0 + (MD_PER_STEP - 1) * max(t2 - t0, 1e-9) / 2.0
+    return sysd.n * MD_PER_STEP / period, t0 + t2, oracle.num_threads(), period
+
+
+SAMPLE_NOTE = ("oracle on all {n} atoms: one re-sort + list build + forces (t0), then the same "
+               "plus 2 velocity-Verlet steps (t2); {w:.1f} s of CPU work; scaled to a 20-step "
+               "period as t0 + 19*(t2-t0)/2")
+
+
+def run_reference(args, dist):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores."""
+    if dist.rank != 0:
+        return 0
+    import md_inputs as mi
+    import oracle
+    sysd = mi.workload(args.workload)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(sysd)
+    periods, work, cores = [], 0.0, 1
+    for _ in range(args.steps):
+        _, w, cores, period = oracle_sample(sysd)
+        periods.append(period)
+        work += w
+    total = sum(periods)
+    value = sysd.n * MD_PER_STEP * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "atoms": sysd.n, "md_steps_per_step": MD_PER_STEP,
+                       "precision": "fp64", "rebuild_every": 20},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": SAMPLE_NOTE.format(n=sysd.n, w=work / args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, dist):
+    import torch
+
+    import md_inputs as mi
+    from paper_2109_09056_b300 import MDSystem
+    from paper_2109_09056_b300 import api as A
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    sysd = mi.workload(args.workload)
+    n = sysd.n
+    stream = torch.cuda.Stream(device=dev)
+    common = dict(rc=sysd.rc, skin=sysd.skin, dt=sysd.dt, rebuild_every=sysd.rebuild_every,
+                  lanes_per_atom=args.lanes, block_threads=args.block, stream=stream)
+
+    # ---- device-resident value (mixed) -------------------------------------
+    sysm = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", **common)
+    sysm.step(MD_PER_STEP * args.warmup)
+    sysm.profile(True)
+    k0 = sysm.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = Clocks(dist.local)
+    e0.record(stream)
+    th = sysm.step(MD_PER_STEP * args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sysm.launch_count() - k0
+    n_force, force_ms, alg_bytes = sysm.profile_read()
+    sysm.profile(False)
+    ms_max = dist.max(ms)
+    value = n * MD_PER_STEP * args.steps * dist.world / (ms_max * 1e-3)
+
+    out = {}
+    pk = peaks()
+    # ---- the FP64 path on the same workload, and mixed-vs-FP64 accuracy -----
+    if not args.no_fp64:
+        s64 = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="fp64", **common)
+        s64.step(MD_PER_STEP)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(MD_PER_STEP)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        v64 = n * MD_PER_STEP / (ms64 * 1e-3)
+        st = sysm.state(device=dev)
+        s64.set_state(st["x"], st["v"])
+        pe_d = s64.compute_forces()
+        pe_m = sysm.compute_forces()
+        fm = sysm.state(device=dev)["f"]
+        f64 = s64.state(device=dev)["f"]
+        rel = float(torch.linalg.norm(fm - f64) / torch.linalg.norm(f64))
+        out["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64,
+                       "mixed_speedup": value / dist.world / v64}
+        out["accuracy"] = {"force_rel_l2_mixed_vs_fp64": rel,
+                           "pe_rel_mixed_vs_fp64": abs(pe_m - pe_d) / abs(pe_d)}
+        s64.close()
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    t_launch = force_ms / max(n_force, 1) * 1e-3
+    hbm_peak = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6400.0
+    achieved = alg_bytes / t_launch / 1e9
+    rec = traffic_record(os.path.join(ROOT, "paper_2109_09056_b300", "csrc", "md_force.cu"))
+    traffic = rec["dram_bytes_per_launch"] * n / rec["atoms"] if rec and rec.get("atoms") else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "k_force_mixed (fused VV)",
+            "peak_source": peak_src, "launch_ms": t_launch * 1e3, "alg_bytes_per_launch": alg_bytes}
+    list_per_atom = (alg_bytes - n * (16 + 16 + 4 + 96 + 16)) / 4.0 / n
+    if clocks and clocks.get("sm_mhz"):
+        sm_mhz = clocks["sm_mhz"]
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        rc_per_atom = list_per_atom * (sysd.rc / (sysd.rc + sysd.skin)) ** 3
+        ops_atom = 10.0 * list_per_atom + 22.0 * rc_per_atom
+        issue = nsm * FP32_LANES_PER_SM * sm_mhz * 1e6
+        roof["alu_view"] = {"achieved_tops": n * ops_atom / t_launch / 1e12,
+                            "peak_tops": issue / 1e12, "frac": n * ops_atom / t_launch / issue,
+                            "sm_mhz": sm_mhz, "ops_per_atom": ops_atom}
+
+    # ---- end to end through the C ABI with pinned host buffers ------------
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(sysd.x).pin_memory()
+        vh = torch.from_numpy(sysd.v).pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        vo = torch.empty_like(vh).pin_memory()
+        se = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", **common)
+        se.set_state(xh, vh)
+        se.step(MD_PER_STEP)
+        torch.cuda.synchronize()
+        dist.barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            se.set_state(xh, vh)                      # H2D of the step's inputs (x, v)
+            se.step(MD_PER_STEP)                      # thermo of the step back to the host
+            A.check(A.lib.md_get_state(se.ctx.handle, A.C.c_void_p(xo.data_ptr()),
+                                       A.C.c_void_p(vo.data_ptr()), None, None, None),
+                    se.ctx.handle)                    # D2H of the step's result (x, v)
+        torch.cuda.synchronize()
+        el = dist.max(time.perf_counter() - t)
+        dist.barrier()
+        e2e = {"value": n * MD_PER_STEP * args.steps * dist.world / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * 8 + vh.numel() * 8),
+               "d2h_bytes_per_step": int(xo.numel() * 8 + vo.numel() * 8 + 112),
+               "ms_per_step": 1e3 * el / args.steps}
+        se.close()
+
+    # ---- CPU baseline (oracle) on rank 0 at N = 1 ---------------------------
+    cpu = None
+    if not args.no_cpu and dist.world == 1 and dist.rank == 0:
+        import oracle
+        oracle.build()
+        v_cpu, work, cores, _ = oracle_sample(sysd)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": SAMPLE_NOTE.format(n=n, w=work)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "atoms": n, "md_steps_per_step": MD_PER_STEP,
+                       "precision": "mixed", "rebuild_every": sysd.rebuild_every,
+                       "lanes_per_atom": args.lanes or 4, "list_entries_per_atom": list_per_atom,
+                       "parallelism": f"replicas x{dist.world}",
+                       "l2": "inputs larger than L2 (list ~2 GB + state ~0.3 GB per replica)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+            "final_thermo": {"pe_per_atom": th["pe"] / n, "temperature": th["temperature"],
+                             "dangerous_builds": th["dangerous_builds"], "nn_max": th["nn_max"]}}
+    line.update(out)
+    sysm.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, dist)
+        return run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -166,6 +166,9 @@ md_status md_force_backward(md_ctx *ctx, const double *dL_dF, double dL_dE, doub
  * (ntypes*ntypes host arrays; NULL keeps the current ones); velocities kept.
  * Follows with the same wrap/sort/build/forces as md_create. */
 md_status md_set_positions(md_ctx *ctx, const double *x);
+/* Replaces positions and velocities (n x 3 each, original order; NULL keeps
+ * the current array) and re-sorts / rebuilds / recomputes forces. */
+md_status md_set_state(md_ctx *ctx, const double *x, const double *v);
 md_status md_set_params(md_ctx *ctx, const double *eps, const double *sigma);
 
 /* Copies the state out in ORIGINAL order: x (n x 3, positions as stored: wrapped
@@ -199,6 +202,10 @@ md_status md_get_thermo_log(md_ctx *ctx, double *rows, int32_t *count);
  * algorithmic count (list entries + positions + state), and resets. */
 md_status md_profile(md_ctx *ctx, int32_t on);
 md_status md_profile_read(md_ctx *ctx, int64_t *launches, double *ms, double *alg_bytes);
+
+/* Number of library kernels enqueued on this context since creation (graph
+ * replays count every kernel node of the replayed graph). */
+md_status md_launch_count(md_ctx *ctx, int64_t *kernels);
 
 const char *md_last_error(const md_ctx *ctx);
 void md_destroy(md_ctx *ctx);

@@ -174,6 +174,8 @@ def workload(name: str) -> LJSystem:
         return lj_melt(32, seed=2)
     if name == "lj_fcc100_4m":
         return lj_melt(100, seed=3, jitter=0.05)
+    if name == "lj_fcc50_500k":         # same recipe at 1/8 size (profiling captures)
+        return lj_melt(50, seed=3, jitter=0.05)
     if name == "lj_2type_fcc20_32000":
         return two_type_melt(20, seed=7)
     raise KeyError(name)

@@ -70,6 +70,7 @@ SIGNATURES = {
     "md_step": ([P, C.c_int32, C.POINTER(md_thermo)], C.c_int),
     "md_force_backward": ([P, P, C.c_double, P, P, P], C.c_int),
     "md_set_positions": ([P, P], C.c_int),
+    "md_set_state": ([P, P, P], C.c_int),
     "md_set_params": ([P, P, P], C.c_int),
     "md_get_state": ([P, P, P, P, P, P], C.c_int),
     "md_get_permutation": ([P, P], C.c_int),
@@ -78,6 +79,7 @@ SIGNATURES = {
     "md_get_thermo_log": ([P, P, C.POINTER(C.c_int32)], C.c_int),
     "md_profile": ([P, C.c_int32], C.c_int),
     "md_profile_read": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "md_launch_count": ([P, C.POINTER(C.c_int64)], C.c_int),
     "md_last_error": ([P], C.c_char_p),
     "md_destroy": ([P], None),
     "md_batch_create": ([C.c_int32, P, P, P, P, P, C.POINTER(md_params), P, C.POINTER(P)], C.c_int),

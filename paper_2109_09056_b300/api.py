@@ -183,6 +183,12 @@ def md_set_positions(ctx: Ctx, x) -> None:
     check(lib.md_set_positions(ctx.handle, px), ctx.handle)
 
 
+def md_set_state(ctx: Ctx, x=None, v=None) -> None:
+    px, kx = _arr(x, np.float64, (ctx.n, 3))
+    pv, kv = _arr(v, np.float64, (ctx.n, 3))
+    check(lib.md_set_state(ctx.handle, px, pv), ctx.handle)
+
+
 def md_set_params(ctx: Ctx, eps=None, sigma=None) -> None:
     pe, ke = _arr(None if eps is None else np.asarray(eps), np.float64)
     ps, ks = _arr(None if sigma is None else np.asarray(sigma), np.float64)
@@ -249,6 +255,12 @@ def md_profile_read(ctx: Ctx) -> tuple:
     return k.value, ms.value, by.value
 
 
+def md_launch_count(ctx: Ctx) -> int:
+    k = C.c_int64()
+    check(lib.md_launch_count(ctx.handle, C.byref(k)), ctx.handle)
+    return k.value
+
+
 def md_info(ctx: Ctx) -> tuple:
     nb = C.c_int32()
     n = C.c_int64()
@@ -301,6 +313,12 @@ class MDSystem:
 
     def set_positions(self, x):
         md_set_positions(self.ctx, x)
+
+    def set_state(self, x=None, v=None):
+        md_set_state(self.ctx, x, v)
+
+    def launch_count(self) -> int:
+        return md_launch_count(self.ctx)
 
     def set_params(self, eps=None, sigma=None):
         md_set_params(self.ctx, eps, sigma)

@@ -60,7 +60,7 @@ void free_all(md_ctx *c) {
     F(c->f); F(c->rbuild); F(c->xw); F(c->xws); F(c->xraw);
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
-    F(c->tpart); F(c->tbox); F(c->tlog); F(c->dscratch); F(c->stage);
+    F(c->tpart); F(c->tbox); F(c->tlog); F(c->dscratch); F(c->stage); F(c->restage);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -576,6 +576,7 @@ static md_status run_period_graph(md_ctx *c) {
     const int key = c->pc * 2 + c->oc;
     const int every = c->params.rebuild_every;
     const int pc0 = c->pc, oc0 = c->oc;
+    const int64_t k0 = c->kernels;
     if (!c->gexec[key]) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -597,8 +598,10 @@ static md_status run_period_graph(md_ctx *c) {
         // capture recorded the parity changes; restore and replay below
         c->pc = pc0;
         c->oc = oc0;
+        c->kernels = k0;
     }
     CK(cudaGraphLaunch(c->gexec[key], c->stream));
+    c->kernels += 5 + 1 + 2 * every;
     c->oc ^= 1;
     if (every % 2) c->pc ^= 1;
     return MD_OK;
@@ -834,30 +837,35 @@ md_status md_force_backward(md_ctx *c, const double *dL_dF, double dL_dE, double
     return MD_OK;
 }
 
-md_status md_set_positions(md_ctx *c, const double *x) {
-    if (!c || !x) return MD_ERR_ARG;
+md_status md_set_state(md_ctx *c, const double *x, const double *v) {
+    if (!c) return MD_ERR_ARG;
+    if (!x && !v) return MD_OK;
     const size_t n = (size_t)c->n_total;
-    // current velocities and types in original order, then reload
-    double *vtmp = nullptr;
-    int32_t *ttmp = nullptr;
-    CK(dalloc(&vtmp, 3 * n));
-    cudaError_t e = dalloc(&ttmp, n);
-    if (e != cudaSuccess) { cudaFree(vtmp); return cuda_fail(c, e, "alloc"); }
-    e = launch_get_state(c, nullptr, vtmp, nullptr, nullptr, nullptr, ttmp);
-    md_status s = MD_OK;
-    if (e != cudaSuccess) s = cuda_fail(c, e, "get_state");
-    if (!s) s = load_state(c, x, vtmp, ttmp);
-    if (!s) {
-        e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
+    // Current state in original order (for whatever is not replaced), kept in
+    // a buffer of its own so that load_state may use the staging buffer.
+    const size_t need = 6 * n * sizeof(double) + n * sizeof(int32_t);
+    if (need > c->restage_bytes) {
+        if (c->restage) cudaFree(c->restage);
+        c->restage = nullptr;
+        c->restage_bytes = 0;
+        CK(cudaMalloc(&c->restage, need));
+        c->restage_bytes = need;
     }
-    cudaFree(vtmp);
-    cudaFree(ttmp);
+    double *xcur = static_cast<double *>(c->restage);
+    double *vcur = xcur + 3 * n;
+    int32_t *tcur = reinterpret_cast<int32_t *>(vcur + 3 * n);
+    CK(launch_get_state(c, x ? nullptr : xcur, v ? nullptr : vcur, nullptr, nullptr, nullptr, tcur));
+    md_status s = load_state(c, x ? x : xcur, v ? v : vcur, tcur);
     if (s) return s;
     invalidate_graphs(c);
     s = sort_build_forces(c, true);
     if (s) return s;
     return pull_thermo(c);
+}
+
+md_status md_set_positions(md_ctx *c, const double *x) {
+    if (!c || !x) return MD_ERR_ARG;
+    return md_set_state(c, x, nullptr);
 }
 
 md_status md_set_params(md_ctx *c, const double *eps, const double *sigma) {
@@ -903,6 +911,12 @@ md_status md_profile_read(md_ctx *c, int64_t *launches, double *ms, double *alg_
     }
     c->prof_launches = 0;
     c->prof_ms = 0.0;
+    return MD_OK;
+}
+
+md_status md_launch_count(md_ctx *c, int64_t *kernels) {
+    if (!c || !kernels) return MD_ERR_ARG;
+    *kernels = c->kernels;
     return MD_OK;
 }
 

@@ -160,12 +160,15 @@ struct md_ctx {
     // host-pointer staging
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    void *restage = nullptr;       // current state in original order (md_set_state)
+    size_t restage_bytes = 0;
 
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     int64_t prof_launches = 0;
+    int64_t kernels = 0;           // library kernels enqueued (see md_launch_count)
     double prof_ms = 0.0;
     double prof_bytes = 0.0;
 

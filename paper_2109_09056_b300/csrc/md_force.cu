@@ -477,6 +477,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     k_force<MIXED, T, ONE><<<(unsigned)grid, c->block, 0, c->stream>>>(a);
+    c->kernels += 1;
     return cudaGetLastError();
 }
 
@@ -532,12 +533,14 @@ cudaError_t launch_kick_drift(md_ctx *c) {
         c->dbox, c->tile_box, c->dpair, c->ns, c->type[c->oc], c->f, c->v[c->oc], c->r[c->pc],
         c->r[c->pc ^ 1], c->sh[c->pc ^ 1], c->dflags);
     c->pc ^= 1;
+    c->kernels += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(md_ctx *c, int mode) {
     k_finalize<<<c->nbox, 256, 0, c->stream>>>(c->dbox, 32 / c->T, c->tpart, c->tbox, c->dflags,
                                                 c->tlog, c->tlog_cap, c->params.thermo_every, mode);
+    c->kernels += 1;
     return cudaGetLastError();
 }
 

@@ -220,6 +220,7 @@ cudaError_t launch_build(md_ctx *c) {
         smem_set = smem;
     }
     k_build<<<c->ncell_tot, kThreads, smem, c->stream>>>(a);
+    c->kernels += 1;
     return cudaGetLastError();
 }
 

@@ -259,6 +259,7 @@ cudaError_t launch_unpack_input(md_ctx *c, const double *x_aos, const double *v_
     k_unpack<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
         c->dbox, c->tile_box, c->ns, x_aos, v_aos, types, c->xraw, c->v[c->oc], c->type[c->oc],
         c->id[c->oc], c->img[c->oc], c->cellc[c->oc]);
+    c->kernels += 1;
     return cudaGetLastError();
 }
 
@@ -282,6 +283,7 @@ cudaError_t launch_bin_sort(md_ctx *c, bool raw_input) {
         c->img[oc], c->r[pc], c->v[oc ^ 1], c->type[oc ^ 1], c->id[oc ^ 1], c->img[oc ^ 1],
         c->cellc[oc ^ 1], c->cellc[oc], c->sh[pc], c->rbuild, c->xws, c->nn, c->dflags);
     c->oc ^= 1;
+    c->kernels += 5;
     return cudaGetLastError();
 }
 
