@@ -227,6 +227,29 @@ md_status md_batch_thermo(md_ctx *ctx, md_thermo *out);
 /* Number of boxes (1 for md_create contexts) and total atoms. */
 md_status md_info(md_ctx *ctx, int32_t *nbox, int64_t *n_total);
 
+/* ---- binning + stable cell-order permutation without any allocation ----
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: code running under an allocator that owns the
+ * device's memory, or a loop that must not pay the device-wide
+ * synchronisation cudaMalloc/cudaFree can trigger.  It computes what
+ * md_bin_sort does for a fresh box (wrap, cell per atom, stable sort by
+ * (cell, input index)) and writes perm[new] = old for the n positions x.
+ *   box, rs      : box edges (each > 2 rs) and the cell-size floor rs = rc + skin;
+ *   x            : n x 3 positions, DEVICE memory, read only;
+ *   perm         : n int32, DEVICE memory, written;
+ *   stream       : cudaStream_t the work is enqueued on (returns without waiting).
+ * It allocates nothing: its intermediates live in one fixed array inside the
+ * library (about 4 MiB, held on every GPU that loads the library until the
+ * process exits).  Limits: n <= 262144 and nc_x*nc_y*nc_z <= 131072, else
+ * MD_ERR_ARG.  Host pointers are rejected (MD_ERR_ARG).  Errors are reported
+ * through md_last_error(NULL).  The first call on a device looks up the
+ * array's device address (a host-side query), so make that first call before
+ * any stream capture.  All calls share the array: calls whose work may
+ * overlap on the GPU (unordered streams) race and must be serialised by the
+ * caller.  Positions must be finite. */
+md_status md_bin_sort_noalloc(const md_box *box, int64_t n, const double *x, double rs,
+                              int32_t *perm, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

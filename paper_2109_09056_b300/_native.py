@@ -85,6 +85,7 @@ SIGNATURES = {
     "md_batch_create": ([C.c_int32, P, P, P, P, P, C.POINTER(md_params), P, C.POINTER(P)], C.c_int),
     "md_batch_thermo": ([P, P], C.c_int),
     "md_info": ([P, C.POINTER(C.c_int32), C.POINTER(C.c_int64)], C.c_int),
+    "md_bin_sort_noalloc": ([C.POINTER(md_box), C.c_int64, P, C.c_double, P, P], C.c_int),
 }
 
 

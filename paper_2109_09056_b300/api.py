@@ -261,6 +261,16 @@ def md_launch_count(ctx: Ctx) -> int:
     return k.value
 
 
+def md_bin_sort_noalloc(box, x, rs: float, perm, stream=None) -> None:
+    """Binning + stable cell-order permutation into the caller's device array
+    `perm` without any device allocation (x and perm must be CUDA tensors)."""
+    b = N.md_box()
+    for d in range(3):
+        b.L[d] = float(box[d])
+    check(lib.md_bin_sort_noalloc(C.byref(b), int(x.shape[0]), C.c_void_p(x.data_ptr()),
+                                  float(rs), C.c_void_p(perm.data_ptr()), _stream_handle(stream)))
+
+
 def md_info(ctx: Ctx) -> tuple:
     nb = C.c_int32()
     n = C.c_int64()

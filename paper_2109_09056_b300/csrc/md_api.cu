@@ -436,6 +436,11 @@ struct OutBuf {
 
 }  // namespace
 
+md_status mdb::set_global_error(md_status s, const std::string &msg) {
+    g_create_error = msg;
+    return s;
+}
+
 extern "C" {
 
 void md_params_default(md_params *p) {

@@ -195,4 +195,6 @@ cudaError_t launch_get_neighbors(md_ctx *c, int32_t *nn_out, int32_t *nbr_out, i
 cudaError_t launch_adjoint(md_ctx *c, const double *G_aos, double gE, double *dx_aos,
                            double *totals_out, double *scratch);
 size_t adjoint_scratch_doubles(md_ctx *c);
+// md_api.cu: record a message for md_last_error(NULL) and return s
+md_status set_global_error(md_status s, const std::string &msg);
 }  // namespace mdb
