@@ -2,6 +2,7 @@
 // host/device pointer handling, and the orchestration of the timestep
 // (paper, Introduction / Fig. 1: neighbor list -> forces -> propagate ->
 // resort; Fig. 4 re-expresses that step as library calls, one call per stage).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -87,7 +88,7 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // Pad after an overflow that needed `maxnn` slots: with an automatic pad, 15%
 // + 16 slack; with an explicit md_params.neigh_pad, just enough (rounded to 8).
 int grown_pad(const md_ctx *c, int maxnn) {
-    return c->params.neigh_pad > 0 ? maxnn : (int)(maxnn * 1.15) + 16;
+    return c->params.neigh_pad > 0 ? maxnn : (int)(maxnn * 1.05) + 8;
 }
 
 void invalidate_graphs(md_ctx *c) {
@@ -145,7 +146,9 @@ md_status setup_pair(md_ctx *c, const double *eps, const double *sigma) {
 }
 
 md_status alloc_list(md_ctx *c, int pad) {
-    c->pad = round_up(pad, 8);
+    // a multiple of 4 T keeps R = pad / T a multiple of the force kernel's
+    // 4-entry batch
+    c->pad = round_up(pad, std::max(8, 4 * c->T));
     c->R = c->pad / c->T;
     const size_t words = (size_t)c->ns * c->pad;
     if (words > c->nbr_words) {
@@ -155,6 +158,7 @@ md_status alloc_list(md_ctx *c, int pad) {
         CK(dalloc(&c->nbr, words));
         c->nbr_words = words;
     }
+    CK(fill_list_sentinel(c));
     invalidate_graphs(c);
     c->list_valid = false;
     return MD_OK;
@@ -315,13 +319,15 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     for (int k = 0; k < 2; ++k) {
         CK(dalloc(&c->r[k], 3 * ns));
         CK(dalloc(&c->v[k], 3 * ns));
-        CK(dalloc(&c->sh[k], ns));
+        CK(dalloc(&c->sh[k], ns + 1));   // slot ns: the dummy the sentinel entry points at
         CK(dalloc(&c->type[k], ns));
         CK(dalloc(&c->id[k], ns));
         CK(dalloc(&c->img[k], 3 * ns));
         CK(dalloc(&c->cellc[k], ns));
         CK(cudaMemset(c->r[k], 0, 3 * ns * sizeof(double)));
         CK(cudaMemset(c->sh[k], 0, ns * sizeof(float4)));
+        const float4 far = make_float4(1e4f, 1e4f, 1e4f, 0.f);
+        CK(cudaMemcpy(c->sh[k] + ns, &far, sizeof(float4), cudaMemcpyHostToDevice));
     }
     CK(dalloc(&c->f, 3 * ns));
     CK(cudaMemset(c->f, 0, 3 * ns * sizeof(double)));
@@ -367,7 +373,7 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     int pad = p.neigh_pad;
     if (pad <= 0) {
         const double mean = 4.18879020478639 * rs * rs * rs * max_rho;
-        pad = (int)(1.3 * mean) + 16;
+        pad = (int)(1.15 * mean) + 8;
     }
     return alloc_list(c, pad);
 }

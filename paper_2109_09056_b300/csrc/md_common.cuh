@@ -84,6 +84,9 @@ struct Flags {
     uint32_t pad_;
 };
 
+// Stencil code of a zero offset (ox = oy = oz = 0).
+constexpr uint32_t kCodeZero = 13;
+
 // The centre of cell (cx, cy, cz) along axis d, computed identically wherever
 // an FP64 position is reconstructed as O + r.
 __device__ __forceinline__ double cell_centre(int c, double h) {
@@ -195,6 +198,12 @@ cudaError_t launch_get_neighbors(md_ctx *c, int32_t *nn_out, int32_t *nbr_out, i
 cudaError_t launch_adjoint(md_ctx *c, const double *G_aos, double gE, double *dx_aos,
                            double *totals_out, double *scratch);
 size_t adjoint_scratch_doubles(md_ctx *c);
+// The list entry that pads rows: the dummy shadow slot ns (kept far from every
+// atom) with a zero offset; a pair evaluated against it is masked by rc.
+inline uint32_t sentinel_entry(const md_ctx *c) {
+    return (uint32_t)c->ns | (kCodeZero << MD_IDX_BITS);
+}
+cudaError_t fill_list_sentinel(md_ctx *c);
 // md_api.cu: record a message for md_last_error(NULL) and return s
 md_status set_global_error(md_status s, const std::string &msg);
 }  // namespace mdb

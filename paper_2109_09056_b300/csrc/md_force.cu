@@ -28,6 +28,8 @@ namespace mdb {
 namespace {
 
 constexpr int kMaxWarps = 16;
+constexpr int kBatch = 4;                     // list entries per lane per batch
+constexpr uint32_t kNoEntry = 0xFFFFFFFFu;   // code 31: zero offset, far position
 
 struct ForceArgs {
     const Box *boxes;
@@ -228,14 +230,29 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
             const double rix = a.r_in[i], riy = a.r_in[a.ns + i], riz = a.r_in[2 * a.ns + i];
             ti = ONE ? 0 : a.type[i];
             double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
-            int q = 0;
-            for (int k = sub; k < ni; k += T, ++q) {
-                const uint32_t e = __ldcs(row + (size_t)q * 32);
-                const uint32_t j = e & MD_IDX_MASK;
-                const double *o = s_offd[wib] + 3 * (e >> MD_IDX_BITS);
-                const double dx = (__ldg(a.r_in + j) + o[0]) - rix;
-                const double dy = (__ldg(a.r_in + a.ns + j) + o[1]) - riy;
-                const double dz = (__ldg(a.r_in + 2 * a.ns + j) + o[2]) - riz;
+            // batches of kBatch entries per lane: list words, then positions, then math
+            const int nq = (ni - sub + T - 1) / T;
+            for (int q0 = 0; q0 < nq; q0 += kBatch) {
+              uint32_t e[kBatch];
+#pragma unroll
+              for (int u = 0; u < kBatch; ++u)
+                  e[u] = (q0 + u < nq) ? __ldcs(row + (size_t)(q0 + u) * 32) : kNoEntry;
+              double xj[kBatch], yj[kBatch], zj[kBatch];
+#pragma unroll
+              for (int u = 0; u < kBatch; ++u) {
+                  const uint32_t j = e[u] & MD_IDX_MASK;
+                  const bool ok = e[u] != kNoEntry;
+                  xj[u] = ok ? __ldg(a.r_in + j) : 1e4;
+                  yj[u] = ok ? __ldg(a.r_in + a.ns + j) : 1e4;
+                  zj[u] = ok ? __ldg(a.r_in + 2 * a.ns + j) : 1e4;
+              }
+#pragma unroll
+              for (int u = 0; u < kBatch; ++u) {
+                const uint32_t j = e[u] & MD_IDX_MASK;
+                const double *o = s_offd[wib] + 3 * ((e[u] >> MD_IDX_BITS) % 27);
+                const double dx = (xj[u] + o[0]) - rix;
+                const double dy = (yj[u] + o[1]) - riy;
+                const double dz = (zj[u] + o[2]) - riz;
                 const double r2 = (dx * dx + dy * dy) + dz * dz;
                 if (r2 < rc2) {
                     double e24, s2, e4, ush;
@@ -254,6 +271,7 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
                     fz -= phi * dz;
                     if (THERMO) pe += 0.5 * (e4 * s6 * (s6 - 1.0) - ush);
                 }
+              }
             }
             Fd[0] = sum_lanes_d<T>(fx);
             Fd[1] = sum_lanes_d<T>(fy);
@@ -295,8 +313,215 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
     }
 }
 
+// ---- mixed-precision kernel with the list streamed through shared memory ----
+//
+// Each warp walks a contiguous run of warp-tiles (the CTA's chunk, warps
+// interleaved, so the CTA's warps share neighbors in L1).  While it evaluates
+// tile t it has its next tile's list rows in flight: cp.async (16-byte,
+// L1-bypassing) copies into a per-warp double buffer, only as many 128-byte
+// rows as the tile's longest row needs.  Neighbor shadows are gathered
+// kBatch at a time per lane.
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Rows [0, rows) of warp-tile wt's list block -> dst (rows * 32 words).
+__device__ __forceinline__ void prefetch_rows(const uint32_t *nbr, int64_t wt, int R, int rows,
+                                              uint32_t *dst, int lane) {
+    const uint32_t *src = nbr + (size_t)wt * R * 32;
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+    for (int c = lane; c < rows * 8; c += 32) cp_async16(s + 16u * c, src + 4 * c);
+}
+
+// List rows a warp-tile needs: its longest row, rounded up to whole batches
+// (rows past an atom's count hold the sentinel entry).
+template <int T>
+__device__ __forceinline__ int tile_rows(int ni) {
+    const int r = __reduce_max_sync(0xffffffffu, (ni + T - 1) / T);
+    return (r + kBatch - 1) / kBatch * kBatch;
+}
+
+template <int T, bool ONE, bool THERMO>
+__device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
+                                           float4 (*s_off)[32], uint32_t *lbuf) {
+    constexpr int A = 32 / T;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, sub = lane % T;
+    const int nwc = blockDim.x >> 5;
+    const int64_t chunk = (a.nwt + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * chunk;
+    const int64_t t1 = min(a.nwt, t0 + chunk);
+    const int nt = a.pair->nt;
+    const float rc2f = a.pair->rc2f;
+    const float e24_0 = tb.fe24[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
+    uint32_t *const buf0 = lbuf + (size_t)wib * 2 * a.R * 32;
+    const int bstride = a.R * 32;
+    int64_t wt = t0 + wib;
+    int rows_cur = 0;
+    if (wt < t1) {
+        rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
+        prefetch_rows(a.nbr, wt, a.R, rows_cur, buf0, lane);
+    }
+    cp_async_commit();
+    int cb = 0;
+    int curbox = -1;
+    for (; wt < t1; wt += nwc) {
+        const int64_t wn = wt + nwc;
+        int rows_next = 0;
+        if (wn < t1) {
+            rows_next = tile_rows<T>(min(__ldg(a.nn + wn * A + lane / T), a.pad));
+            prefetch_rows(a.nbr, wn, a.R, rows_next, buf0 + (cb ^ 1) * bstride, lane);
+        }
+        cp_async_commit();
+        const int64_t i = wt * A + lane / T;
+        const int b = a.tile_box[(wt * A) >> 5];
+        const Box &B = a.boxes[b];
+        if (b != curbox) {
+            if (lane >= 27) {
+                s_off[wib][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+                s_off[wib][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
+                                               (float)oz * B.hf[2], 0.f);
+            }
+            curbox = b;
+        }
+        const bool valid = (i - B.slot_off) < B.n;
+        const float4 si = a.sh_in[i];
+        const int ti = ONE ? 0 : __float_as_int(si.w);
+        cp_async_wait<1>();  // this lane's copies of the current tile have landed
+        __syncwarp();        // ... and every other lane's; s_off is visible too
+        const uint32_t *Lr = buf0 + cb * bstride + lane;
+        float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
+        // Whole batches up to the tile's row count; entries past this lane's
+        // count are sentinels (far dummy), masked like any pair beyond rc.
+        for (int q0 = 0; q0 < rows_cur; q0 += kBatch) {
+            uint32_t e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = Lr[(q0 + u) * 32];
+            float4 sj[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (e[u] & MD_IDX_MASK));
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const float4 o = s_off[wib][e[u] >> MD_IDX_BITS];
+                const float dx = (sj[u].x + o.x) - si.x;
+                const float dy = (sj[u].y + o.y) - si.y;
+                const float dz = (sj[u].z + o.z) - si.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool in = r2 < rc2f;
+                float e24, s2, e4, ush;
+                if (ONE) {
+                    e24 = e24_0; s2 = s2_0; e4 = e4_0; ush = ush_0;
+                } else {
+                    const int ab = ti * nt + __float_as_int(sj[u].w);
+                    e24 = tb.fe24[ab]; s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
+                }
+                const float r2inv = __fdividef(1.0f, r2);
+                const float q2 = s2 * r2inv;
+                const float s6 = q2 * q2 * q2;
+                const float phi = in ? e24 * r2inv * s6 * fmaf(2.0f, s6, -1.0f) : 0.0f;
+                kahan_add(fx, cx, -phi * dx);
+                kahan_add(fy, cy, -phi * dy);
+                kahan_add(fz, cz, -phi * dz);
+                if (THERMO) kahan_add(pe, cp, in ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f);
+            }
+        }
+        __syncwarp();  // done reading buf[cb]; the next prefetch may refill it
+        merge_lanes<T>(fx, cx);
+        merge_lanes<T>(fy, cy);
+        merge_lanes<T>(fz, cz);
+        double ped = 0.0;
+        if (THERMO) {
+            merge_lanes<T>(pe, cp);
+            ped = (double)pe;
+        }
+        // Epilogue: one FP64 update per component, the components spread over
+        // the atom's lanes (lane sub takes components sub, sub + T, ...).
+        double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
+        float snew[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < (3 + T - 1) / T; ++k) {
+            const int d = sub + k * T;
+            if (valid && d < 3) {
+                const float Fs = d == 0 ? fx : (d == 1 ? fy : fz);
+                double pp = 0.0;
+                const float sn = epilogue<THERMO>(a, tb, i, d, ti, (double)Fs, ke, pp, disp2);
+#pragma unroll
+                for (int dd = 0; dd < 3; ++dd)
+                    if (dd == d) { snew[dd] = sn; pd[dd] = pp; }
+            }
+        }
+        if (a.mode == MODE_FUSED) {
+            float s3[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                s3[d] = __shfl_sync(0xffffffffu, snew[d], (lane - sub) + d % T);
+            if (valid && sub == 0) a.sh_out[i] = make_float4(s3[0], s3[1], s3[2], __int_as_float(ti));
+        }
+        if (THERMO) {
+            const double dsum = sum_lanes_d<T>(disp2);
+            const double pe_t = warp_sum_d((valid && sub == 0) ? ped : 0.0);
+            const double ke_t = warp_sum_d(ke);
+            const double px = warp_sum_d(pd[0]), py = warp_sum_d(pd[1]), pz = warp_sum_d(pd[2]);
+            const double dm = warp_max_d(valid ? dsum : 0.0);
+            if (lane == 0) {
+                double *tp = a.tpart + wt * TP;
+                tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
+            }
+        }
+        cb ^= 1;
+        rows_cur = rows_next;
+    }
+    cp_async_wait<0>();
+}
+
+template <int T, bool ONE>
+__global__ void __launch_bounds__(128, 5) k_force_mixed(ForceArgs a) {
+    if (a.fl->status & ST_FREEZE) {
+        if (a.mode == MODE_FUSED) {
+            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
+                 t += (int64_t)gridDim.x * blockDim.x) {
+                a.sh_out[t] = a.sh_in[t];
+                for (int d = 0; d < 3; ++d) a.r_out[d * a.ns + t] = a.r_in[d * a.ns + t];
+            }
+        }
+        return;
+    }
+    extern __shared__ __align__(16) uint32_t lbuf[];
+    __shared__ SmemTabs tb;
+    __shared__ __align__(16) float4 s_off[4][32];
+    const Pair &P = *a.pair;
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+        tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
+        if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
+    }
+    __syncthreads();
+    const int64_t clock = a.fl->clock;
+    const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
+    if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, lbuf);
+    else mixed_body<T, ONE, false>(a, tb, s_off, lbuf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(a.done, 1u);
+        if (prev == gridDim.x - 1) {
+            *a.done = 0u;
+            a.fl->thermo = thermo ? 1u : 0u;
+            if (a.mode == MODE_FUSED) a.fl->clock = clock + 1;
+        }
+    }
+}
+
 template <bool MIXED, int T, bool ONE>
-__global__ void __launch_bounds__(256) k_force(ForceArgs a) {
+__global__ void __launch_bounds__(256, 2) k_force(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
         // Frozen (a list overflowed earlier in this run): keep the state and
         // mirror it into the output buffers so the buffer flip stays valid.
@@ -462,6 +687,34 @@ __global__ void k_get_neighbors(const Box *__restrict__ boxes, const int32_t *__
 
 template <bool MIXED, int T, bool ONE>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
+    if (MIXED) {
+        // 4 warps per CTA, each with a double buffer of R list rows.
+        const int block = 128;
+        const size_t smem = (size_t)4 * 2 * a.R * 32 * sizeof(uint32_t);
+        static size_t smem_set = 0, occ_smem = 0;
+        static int occ = 0;
+        if (smem > smem_set) {
+            cudaError_t e = cudaFuncSetAttribute(
+                k_force_mixed<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            smem_set = smem;
+        }
+        if (occ_smem != smem) {
+            int per = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per, k_force_mixed<T, ONE>, block, smem);
+            if (e != cudaSuccess) return e;
+            occ = per > 0 ? per : 1;
+            occ_smem = smem;
+        }
+        int64_t grid = (int64_t)c->nsm * occ;
+        const int64_t need = (a.nwt + 3) / 4;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
+        c->kernels += 1;
+        return cudaGetLastError();
+    }
     static int grid_cache[2][9][2][9] = {};
     int &g = grid_cache[MIXED][T][ONE][(c->block / 32) & 7];
     if (g == 0) {

@@ -21,6 +21,8 @@
 // slots hold the same cell under two images; only one image can lie within
 // rs (L > 2 rs), and the FP64 re-test checks that the slot's image is the
 // nearest one.
+#include <algorithm>
+
 #include "md_common.cuh"
 
 namespace mdb {
@@ -40,6 +42,7 @@ struct BuildArgs {
     double rs2;
     float rs2f, bandf;
     int pad, R, T;
+    uint32_t sentinel;
     int32_t *nn;
     uint32_t *nbr;
     Flags *fl;
@@ -168,11 +171,13 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
             if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
         }
         __syncthreads();
-        // Write the rows of this chunk: warp-tiles W0..W1, rows q < ceil(maxE / T);
-        // each store is one 32-word row (lanes outside the chunk masked).
+        // Write the rows of this chunk: warp-tiles W0..W1, all R rows; each
+        // store is one 32-word row (lanes of atoms outside the chunk masked).
+        // Slots past an atom's count get the sentinel entry (a dummy slot far
+        // away, zero offset), so readers may run whole batches unpredicated.
         const int64_t first = h0 + hc, last = h0 + hc + na - 1;
         const int64_t W0 = first / A, W1 = last / A;
-        const int rows = (s_maxe + T - 1) / T;
+        const int rows = a.R;
         const int64_t items = (W1 - W0 + 1) * rows;
         for (int64_t it = wib; it < items; it += NW) {
             const int64_t W = W0 + it / rows;
@@ -180,14 +185,31 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
             const int64_t i = W * A + lane / T;
             const int64_t ha = i - first;
             const int k = q * T + lane % T;
-            if (ha >= 0 && ha < na && k < min(s_cnt[ha], a.pad))
-                a.nbr[((size_t)W * a.R + q) * 32 + lane] = lst[ha * a.pad + k];
+            if (ha >= 0 && ha < na)
+                a.nbr[((size_t)W * a.R + q) * 32 + lane] =
+                    k < min(s_cnt[ha], a.pad) ? lst[ha * a.pad + k] : a.sentinel;
         }
         __syncthreads();
     }
 }
 
+__global__ void k_fill_u32(uint32_t *__restrict__ p, size_t n, uint32_t v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 }  // namespace
+
+// Every list slot (including the rows of padding slots, which no build
+// writes) starts as the sentinel entry.
+cudaError_t fill_list_sentinel(md_ctx *c) {
+    const size_t words = (size_t)c->ns * c->pad;
+    k_fill_u32<<<(unsigned)std::min<size_t>((words + 255) / 256, 65535), 256, 0, c->stream>>>(
+        c->nbr, words, sentinel_entry(c));
+    c->kernels += 1;
+    return cudaGetLastError();
+}
 
 size_t build_smem_bytes(int pad) {
     return (size_t)kMaxCand * (sizeof(float4) + sizeof(uint32_t)) +
@@ -208,6 +230,7 @@ cudaError_t launch_build(md_ctx *c) {
     a.pad = c->pad;
     a.R = c->R;
     a.T = c->T;
+    a.sentinel = sentinel_entry(c);
     a.nn = c->nn;
     a.nbr = c->nbr;
     a.fl = c->dflags;
