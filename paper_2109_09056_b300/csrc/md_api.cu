@@ -61,7 +61,8 @@ void free_all(md_ctx *c) {
     F(c->f); F(c->rbuild); F(c->xw); F(c->xws); F(c->xraw);
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
-    F(c->tpart); F(c->tbox); F(c->tlog); F(c->dscratch); F(c->stage); F(c->restage);
+    F(c->tpart); F(c->tbox); F(c->fpart); F(c->tlog); F(c->dscratch); F(c->stage);
+    F(c->restage);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -148,7 +149,7 @@ md_status setup_pair(md_ctx *c, const double *eps, const double *sigma) {
 md_status alloc_list(md_ctx *c, int pad) {
     // a multiple of 4 T keeps R = pad / T a multiple of the force kernel's
     // 4-entry batch
-    c->pad = round_up(pad, std::max(8, 4 * c->T));
+    c->pad = round_up(pad, std::max(8, MD_FORCE_BATCH * c->T));
     c->R = c->pad / c->T;
     const size_t words = (size_t)c->ns * c->pad;
     if (words > c->nbr_words) {
@@ -362,6 +363,13 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     CK(cudaMemset(c->dflags, 0, sizeof(Flags)));
     CK(dalloc(&c->tpart, ns * TP));  // enough for T = 1 (one warp-tile per 32 slots ... ns/A tiles)
     CK(dalloc(&c->tbox, (size_t)nbox * TB));
+    {
+        // first-level thermo CTAs per box: ~2048 warp-tiles each, 1..64
+        int64_t maxslots = 0;
+        for (const Box &B : c->hbox) maxslots = std::max<int64_t>(maxslots, B.npad);
+        c->fsplit = (int)std::min<int64_t>(64, std::max<int64_t>(1, maxslots / 8 / 2048));
+        CK(dalloc(&c->fpart, (size_t)nbox * c->fsplit * 6));
+    }
     CK(cudaMemset(c->tbox, 0, sizeof(double) * TB * nbox));
     c->tlog_cap = 4096;
     CK(dalloc(&c->tlog, (size_t)c->tlog_cap * 4));
@@ -609,10 +617,11 @@ static md_status run_period_graph(md_ctx *c) {
         // capture recorded the parity changes; restore and replay below
         c->pc = pc0;
         c->oc = oc0;
+        c->graph_nk[key] = c->kernels - k0;
         c->kernels = k0;
     }
     CK(cudaGraphLaunch(c->gexec[key], c->stream));
-    c->kernels += 5 + 1 + 2 * every;
+    c->kernels += c->graph_nk[key];
     c->oc ^= 1;
     if (every % 2) c->pc ^= 1;
     return MD_OK;

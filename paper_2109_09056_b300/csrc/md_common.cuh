@@ -31,6 +31,15 @@
 #define MD_IDX_BITS 27
 #define MD_IDX_MASK 0x07FFFFFFu
 
+// Compile-time tuning of the mixed force kernel: list entries each lane takes
+// per batch, and the resident CTAs per SM its register budget is sized for.
+#ifndef MD_FORCE_BATCH
+#define MD_FORCE_BATCH 4
+#endif
+#ifndef MD_FORCE_MINB
+#define MD_FORCE_MINB 5
+#endif
+
 namespace mdb {
 
 enum : uint32_t { ST_OVERFLOW = 1u, ST_NONFINITE = 2u };
@@ -140,6 +149,8 @@ struct md_ctx {
     mdb::Flags *dflags = nullptr;
     double *tpart = nullptr;       // ns/ (32/T) warp tiles * TP  (allocated for T = 1: ns * TP)
     double *tbox = nullptr;        // nbox * TB
+    double *fpart = nullptr;       // nbox * fsplit * 6: first-level thermo sums
+    int fsplit = 1;                // CTAs per box in the first thermo level
     double *tlog = nullptr;        // log rows * 4
     int32_t tlog_cap = 0;
     double *dscratch = nullptr;    // adjoint partials etc.
@@ -158,6 +169,7 @@ struct md_ctx {
 
     // graphs: one executable per (pc, oc) parity at the start of a period
     cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t graph_nk[4] = {0, 0, 0, 0};   // kernels in each captured graph
     int64_t built_at = -1;         // step at which the current list was built
     bool forces_valid = false;
     // host-pointer staging

@@ -28,7 +28,7 @@ namespace mdb {
 namespace {
 
 constexpr int kMaxWarps = 16;
-constexpr int kBatch = 4;                     // list entries per lane per batch
+constexpr int kBatch = MD_FORCE_BATCH;        // list entries per lane per batch
 constexpr uint32_t kNoEntry = 0xFFFFFFFFu;   // code 31: zero offset, far position
 
 struct ForceArgs {
@@ -484,7 +484,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
 }
 
 template <int T, bool ONE>
-__global__ void __launch_bounds__(128, 5) k_force_mixed(ForceArgs a) {
+__global__ void __launch_bounds__(128, MD_FORCE_MINB) k_force_mixed(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
         if (a.mode == MODE_FUSED) {
             for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
@@ -591,48 +591,64 @@ __global__ void k_kick_drift(const Box *__restrict__ boxes, const int32_t *__res
     sh_out[i] = make_float4(s[0], s[1], s[2], __int_as_float(ty));
 }
 
-// One CTA per box: fixed-order reduction of the warp-tile partials.
-__global__ void __launch_bounds__(256) k_finalize(const Box *__restrict__ boxes, int A,
-                                                  const double *__restrict__ tpart,
-                                                  double *__restrict__ tbox, Flags *fl,
-                                                  double *__restrict__ tlog, int32_t tlog_cap,
-                                                  int thermo_every, int mode) {
+// Thermo reduction in two fixed-order levels: CTA (b, s) sums the s-th of
+// `split` contiguous ranges of box b's warp-tile partials; then one CTA per box
+// sums its `split` results in order.  Deterministic for a given split.
+__global__ void __launch_bounds__(256) k_finalize_part(const Box *__restrict__ boxes, int A,
+                                                       int split, const double *__restrict__ tpart,
+                                                       double *__restrict__ fpart, const Flags *fl) {
     if (fl->status & ST_FREEZE) return;
     if (fl->thermo == 0u) return;  // the force kernel computed no thermo this step
-    const int b = blockIdx.x;
+    const int b = blockIdx.x / split, s = blockIdx.x % split;
     const Box &B = boxes[b];
     const int64_t w0 = B.slot_off / A, w1 = (B.slot_off + B.npad) / A;
+    const int64_t chunk = (w1 - w0 + split - 1) / split;
+    const int64_t lo = w0 + s * chunk, hi = min(w1, lo + chunk);
     __shared__ double red[6][256];
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+    for (int64_t w = lo + threadIdx.x; w < hi; w += blockDim.x) {
         const double *tp = tpart + w * TP;
         for (int q = 0; q < 5; ++q) acc[q] += tp[q];
         acc[5] = fmax(acc[5], tp[5]);
     }
     for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = acc[q];
     __syncthreads();
-    for (int s = 128; s >= 1; s >>= 1) {
-        if (threadIdx.x < s) {
-            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
-            red[5][threadIdx.x] = fmax(red[5][threadIdx.x], red[5][threadIdx.x + s]);
+    for (int h = 128; h >= 1; h >>= 1) {
+        if (threadIdx.x < h) {
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+            red[5][threadIdx.x] = fmax(red[5][threadIdx.x], red[5][threadIdx.x + h]);
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        // step the numbers describe: FUSED already advanced the clock
-        const int64_t step = fl->clock - (mode == MODE_FUSED ? 1 : 0);
-        double *tb = tbox + b * TB;
-        for (int q = 0; q < 5; ++q) tb[q] = red[q][0];
-        tb[5] = sqrt(red[5][0]);
-        tb[6] = (double)step;
-        if (b == 0 && thermo_every > 0 && step % thermo_every == 0) {
-            const int64_t row = step / thermo_every;
-            if (row < tlog_cap) {
-                tlog[4 * row + 0] = (double)step;
-                tlog[4 * row + 1] = red[0][0];
-                tlog[4 * row + 2] = red[1][0];
-                tlog[4 * row + 3] = red[0][0] + red[1][0];
-            }
+    if (threadIdx.x < 6) fpart[(size_t)blockIdx.x * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_finalize(int split, const double *__restrict__ fpart,
+                           double *__restrict__ tbox, Flags *fl, double *__restrict__ tlog,
+                           int32_t tlog_cap, int thermo_every, int mode) {
+    if (fl->status & ST_FREEZE) return;
+    if (fl->thermo == 0u) return;
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < split; ++s) {
+        const double *p = fpart + ((size_t)b * split + s) * 6;
+        for (int q = 0; q < 5; ++q) acc[q] += p[q];
+        acc[5] = fmax(acc[5], p[5]);
+    }
+    // step the numbers describe: FUSED already advanced the clock
+    const int64_t step = fl->clock - (mode == MODE_FUSED ? 1 : 0);
+    double *tb = tbox + b * TB;
+    for (int q = 0; q < 5; ++q) tb[q] = acc[q];
+    tb[5] = sqrt(acc[5]);
+    tb[6] = (double)step;
+    if (b == 0 && thermo_every > 0 && step % thermo_every == 0) {
+        const int64_t row = step / thermo_every;
+        if (row < tlog_cap) {
+            tlog[4 * row + 0] = (double)step;
+            tlog[4 * row + 1] = acc[0];
+            tlog[4 * row + 2] = acc[1];
+            tlog[4 * row + 3] = acc[0] + acc[1];
         }
     }
 }
@@ -791,9 +807,11 @@ cudaError_t launch_kick_drift(md_ctx *c) {
 }
 
 cudaError_t launch_finalize(md_ctx *c, int mode) {
-    k_finalize<<<c->nbox, 256, 0, c->stream>>>(c->dbox, 32 / c->T, c->tpart, c->tbox, c->dflags,
-                                                c->tlog, c->tlog_cap, c->params.thermo_every, mode);
-    c->kernels += 1;
+    k_finalize_part<<<c->nbox * c->fsplit, 256, 0, c->stream>>>(c->dbox, 32 / c->T, c->fsplit,
+                                                                 c->tpart, c->fpart, c->dflags);
+    k_finalize<<<c->nbox, 32, 0, c->stream>>>(c->fsplit, c->fpart, c->tbox, c->dflags, c->tlog,
+                                              c->tlog_cap, c->params.thermo_every, mode);
+    c->kernels += 2;
     return cudaGetLastError();
 }
 

@@ -2,13 +2,14 @@
 // List Creation": "traditional binning methods used in many MD applications
 // (Verlet lists)", stored in a dense padded format).
 //
-// One CTA per cell.  The CTA stages the candidates of the 27-cell stencil in
-// shared memory (FP32 cell-local coordinates shifted by the stencil offset, so
-// a candidate's coordinate is relative to the home cell's centre), then each
-// warp takes one home atom at a time and its 32 lanes test 32 candidates per
-// step; accepted candidates are compacted with a ballot into the atom's row
-// (staged in shared memory) and finally written out in the warp-transposed
-// padded layout with full 128-byte row stores.
+// One warp per cell, one lane per home atom.  The warp stages the candidates
+// of the cell's 27-cell stencil in its own shared-memory window (FP32
+// cell-local coordinates shifted by the stencil offset, so a candidate's
+// coordinate is relative to the home cell's centre); then every lane walks
+// the window in order -- all lanes read the same candidate, a broadcast -- and
+// appends accepted neighbors straight into its own row of the warp-transposed
+// padded list.  The list is pre-filled with the sentinel entry, so slots past
+// an atom's count need no write.
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
 // the nearest-image FP64 distance r^2 = (dx*dx + dy*dy) + dz*dz, every op
@@ -28,9 +29,8 @@
 namespace mdb {
 namespace {
 
-constexpr int kMaxCand = 1024;  // candidates staged per window
-constexpr int kHome = 32;       // home atoms per chunk
-constexpr int kThreads = 128;
+constexpr int kWarps = 4;       // cells per CTA (one warp each)
+constexpr int kCand = 640;      // candidates staged per warp per window
 
 struct BuildArgs {
     const Box *boxes;
@@ -39,10 +39,10 @@ struct BuildArgs {
     const float4 *sh;
     const double *xws;
     int64_t ns;
+    int32_t ncell;
     double rs2;
     float rs2f, bandf;
-    int pad, R, T;
-    uint32_t sentinel;
+    int pad, R;
     int32_t *nn;
     uint32_t *nbr;
     Flags *fl;
@@ -67,129 +67,117 @@ __device__ __forceinline__ bool exact_test(const BuildArgs &a, const Box &B, int
     return same_image && (r2 < a.rs2);
 }
 
-__global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
+template <int T>
+__global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
+    constexpr int A = 32 / T;
     if (a.fl->status & ST_FREEZE) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float4 *cpos = reinterpret_cast<float4 *>(smem);
-    uint32_t *cmeta = reinterpret_cast<uint32_t *>(cpos + kMaxCand);
-    uint32_t *lst = cmeta + kMaxCand;  // kHome * pad
-    __shared__ int64_t s_start[27];
-    __shared__ int32_t s_pref[28];
-    __shared__ float4 s_off[27];
-    __shared__ int32_t s_cnt[kHome];
-    __shared__ int32_t s_maxe;
-
-    const int c = blockIdx.x;
+    __shared__ __align__(16) float4 cand[kWarps][kCand];
+    __shared__ int64_t s_start[kWarps][27];
+    __shared__ int32_t s_pref[kWarps][28];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * kWarps + w;
+    if (c >= a.ncell) return;  // whole warp
     const Box &B = a.boxes[a.cell_box[c]];
     const int64_t base = (int64_t)B.slot_off - B.atom_base;
     const int hm = a.cstart[c + 1] - a.cstart[c];
-    if (hm == 0) return;
+    if (hm == 0) return;  // whole warp
     const int64_t h0 = base + a.cstart[c];
-    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    constexpr int NW = kThreads / 32;
-
-    if (tid < 27) {
+    // stencil slots: first slot and count of each of the 27 cells
+    int cnt_s = 0;
+    if (lane < 27) {
         const int loc = c - B.cell_off;
-        const int cx = loc % B.nc[0], cy = (loc / B.nc[0]) % B.nc[1],
-                  cz = loc / (B.nc[0] * B.nc[1]);
-        const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
-        const int nx = (cx + ox + B.nc[0]) % B.nc[0];
-        const int ny = (cy + oy + B.nc[1]) % B.nc[1];
-        const int nz = (cz + oz + B.nc[2]) % B.nc[2];
-        const int nc = B.cell_off + (nz * B.nc[1] + ny) * B.nc[0] + nx;
-        s_start[tid] = base + a.cstart[nc];
-        s_pref[tid + 1] = a.cstart[nc + 1] - a.cstart[nc];
-        s_off[tid] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1], (float)oz * B.hf[2], 0.f);
+        const int cx = loc % B.nc[0], cy = (loc / B.nc[0]) % B.nc[1], cz = loc / (B.nc[0] * B.nc[1]);
+        const int nx = (cx + lane % 3 - 1 + B.nc[0]) % B.nc[0];
+        const int ny = (cy + (lane / 3) % 3 - 1 + B.nc[1]) % B.nc[1];
+        const int nz = (cz + lane / 9 - 1 + B.nc[2]) % B.nc[2];
+        const int ncl = B.cell_off + (nz * B.nc[1] + ny) * B.nc[0] + nx;
+        s_start[w][lane] = base + a.cstart[ncl];
+        cnt_s = a.cstart[ncl + 1] - a.cstart[ncl];
     }
-    __syncthreads();
-    if (tid == 0) {
-        s_pref[0] = 0;
-        for (int s = 0; s < 27; ++s) s_pref[s + 1] += s_pref[s];
+    int incl = cnt_s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    __syncthreads();
-    const int M = s_pref[27];
-    const int nwin = (M + kMaxCand - 1) / kMaxCand;
-    const int T = a.T, A = 32 / T;
+    if (lane < 27) s_pref[w][lane + 1] = incl;
+    if (lane == 0) s_pref[w][0] = 0;
+    const int M = __shfl_sync(0xffffffffu, incl, 26);
+    __syncwarp();
 
-    for (int hc = 0; hc < hm; hc += kHome) {
-        const int na = min(kHome, hm - hc);
-        if (tid < kHome) s_cnt[tid] = 0;
-        if (tid == 0) s_maxe = 0;
-        for (int w = 0; w < nwin; ++w) {
-            const int w0 = w * kMaxCand;
-            const int Mw = min(kMaxCand, M - w0);
-            if (nwin > 1 || hc == 0) {
-                __syncthreads();
-                for (int k = tid; k < Mw; k += kThreads) {
-                    const int g = w0 + k;
-                    int s = 0;
-                    while (s_pref[s + 1] <= g) ++s;
-                    const int64_t j = s_start[s] + (g - s_pref[s]);
+    for (int hb = 0; hb < hm; hb += 32) {
+        const int ha = hb + lane;
+        const bool active = ha < hm;
+        const int64_t i = h0 + (active ? ha : 0);
+        const float4 si = a.sh[i];
+        int cnt = 0;
+        // this lane's row: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
+        uint32_t *rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
+        for (int w0 = 0; w0 < M; w0 += kCand) {
+            const int Mw = min(kCand, M - w0);
+            __syncwarp();
+            for (int s = 0; s < 27; ++s) {
+                const int lo = max(s_pref[w][s], w0), hi = min(s_pref[w][s + 1], w0 + Mw);
+                const float ox = (float)(s % 3 - 1) * B.hf[0];
+                const float oy = (float)((s / 3) % 3 - 1) * B.hf[1];
+                const float oz = (float)(s / 9 - 1) * B.hf[2];
+                for (int g = lo + lane; g < hi; g += 32) {
+                    const int64_t j = s_start[w][s] + (g - s_pref[w][s]);
                     const float4 p = a.sh[j];
-                    const float4 o = s_off[s];
-                    cpos[k] = make_float4(p.x + o.x, p.y + o.y, p.z + o.z, 0.f);
-                    cmeta[k] = (uint32_t)j | ((uint32_t)s << MD_IDX_BITS);
+                    cand[w][g - w0] = make_float4(
+                        p.x + ox, p.y + oy, p.z + oz,
+                        __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));
                 }
             }
-            __syncthreads();
-            for (int ha = wib; ha < na; ha += NW) {
-                const int64_t i = h0 + hc + ha;
-                const float4 si = a.sh[i];
-                int cnt = s_cnt[ha];
-                for (int kb = 0; kb < Mw; kb += 32) {
-                    const int k = kb + lane;
-                    bool acc = false;
-                    uint32_t meta = 0;
-                    if (k < Mw) {
-                        const float4 p = cpos[k];
-                        meta = cmeta[k];
-                        const int64_t j = meta & MD_IDX_MASK;
-                        const float dx = p.x - si.x, dy = p.y - si.y, dz = p.z - si.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (j != i) {
-                            if (r2 < a.rs2f - a.bandf) acc = true;
-                            else if (r2 <= a.rs2f + a.bandf) acc = exact_test(a, B, i, j, dx, dy, dz);
-                        }
+            __syncwarp();
+            if (active) {
+                const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
+                // accept candidate p (already known to be within the band's top)
+                auto take = [&](const float4 &p, float dx, float dy, float dz, float r2) {
+                    const uint32_t meta = __float_as_uint(p.w);
+                    const int64_t j = meta & MD_IDX_MASK;
+                    bool acc = j != i;
+                    if (acc && r2 >= lo) acc = exact_test(a, B, i, j, dx, dy, dz);
+                    if (acc) {
+                        if (cnt < a.pad) rowp[(cnt / T) * 32 + (cnt % T)] = meta;
+                        ++cnt;
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, acc);
-                    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                    if (acc && pos < a.pad) lst[ha * a.pad + pos] = meta;
-                    cnt += __popc(m);
+                };
+                int k = 0;
+                // four independent distance tests per step, appended in order
+                for (; k + 4 <= Mw; k += 4) {
+                    float4 p[4];
+                    float dx[4], dy[4], dz[4], r2[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        p[u] = cand[w][k + u];
+                        dx[u] = p[u].x - si.x;
+                        dy[u] = p[u].y - si.y;
+                        dz[u] = p[u].z - si.z;
+                        r2[u] = fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u]));
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (r2[u] <= hi) take(p[u], dx[u], dy[u], dz[u], r2[u]);
                 }
-                if (lane == 0) s_cnt[ha] = cnt;
-                __syncwarp();
+                for (; k < Mw; ++k) {
+                    const float4 p = cand[w][k];
+                    const float dx = p.x - si.x, dy = p.y - si.y, dz = p.z - si.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (r2 <= hi) take(p, dx, dy, dz, r2);
+                }
             }
         }
-        __syncthreads();
-        if (tid < na) {
-            const int cnt = s_cnt[tid];
-            const int64_t i = h0 + hc + tid;
+        if (active) {
             a.nn[i] = cnt;
-            atomicMax(&a.fl->maxnn, cnt);
-            atomicAdd(&a.fl->sumnn, (unsigned long long)cnt);
-            atomicMax(&s_maxe, min(cnt, a.pad));
             if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
         }
-        __syncthreads();
-        // Write the rows of this chunk: warp-tiles W0..W1, all R rows; each
-        // store is one 32-word row (lanes of atoms outside the chunk masked).
-        // Slots past an atom's count get the sentinel entry (a dummy slot far
-        // away, zero offset), so readers may run whole batches unpredicated.
-        const int64_t first = h0 + hc, last = h0 + hc + na - 1;
-        const int64_t W0 = first / A, W1 = last / A;
-        const int rows = a.R;
-        const int64_t items = (W1 - W0 + 1) * rows;
-        for (int64_t it = wib; it < items; it += NW) {
-            const int64_t W = W0 + it / rows;
-            const int q = (int)(it % rows);
-            const int64_t i = W * A + lane / T;
-            const int64_t ha = i - first;
-            const int k = q * T + lane % T;
-            if (ha >= 0 && ha < na)
-                a.nbr[((size_t)W * a.R + q) * 32 + lane] =
-                    k < min(s_cnt[ha], a.pad) ? lst[ha * a.pad + k] : a.sentinel;
+        const int mx = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
+        const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt : 0u);
+        if (lane == 0) {
+            atomicMax(&a.fl->maxnn, mx);
+            atomicAdd(&a.fl->sumnn, (unsigned long long)sm);
         }
-        __syncthreads();
     }
 }
 
@@ -199,10 +187,17 @@ __global__ void k_fill_u32(uint32_t *__restrict__ p, size_t n, uint32_t v) {
         p[i] = v;
 }
 
+template <int T>
+cudaError_t launch_build_t(md_ctx *c, const BuildArgs &a) {
+    const unsigned grid = (unsigned)((c->ncell_tot + kWarps - 1) / kWarps);
+    k_build<T><<<grid, kWarps * 32, 0, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // Every list slot (including the rows of padding slots, which no build
-// writes) starts as the sentinel entry.
+// writes) holds the sentinel entry unless a build wrote a neighbor there.
 cudaError_t fill_list_sentinel(md_ctx *c) {
     const size_t words = (size_t)c->ns * c->pad;
     k_fill_u32<<<(unsigned)std::min<size_t>((words + 255) / 256, 65535), 256, 0, c->stream>>>(
@@ -211,10 +206,7 @@ cudaError_t fill_list_sentinel(md_ctx *c) {
     return cudaGetLastError();
 }
 
-size_t build_smem_bytes(int pad) {
-    return (size_t)kMaxCand * (sizeof(float4) + sizeof(uint32_t)) +
-           (size_t)kHome * pad * sizeof(uint32_t);
-}
+size_t build_smem_bytes(int) { return 0; }
 
 cudaError_t launch_build(md_ctx *c) {
     BuildArgs a;
@@ -224,27 +216,27 @@ cudaError_t launch_build(md_ctx *c) {
     a.sh = c->sh[c->pc];
     a.xws = c->xws;
     a.ns = c->ns;
+    a.ncell = c->ncell_tot;
     a.rs2 = c->hpair.rs2;
     a.rs2f = c->hpair.rs2f;
     a.bandf = c->hpair.bandf;
     a.pad = c->pad;
     a.R = c->R;
-    a.T = c->T;
-    a.sentinel = sentinel_entry(c);
     a.nn = c->nn;
     a.nbr = c->nbr;
     a.fl = c->dflags;
-    const size_t smem = build_smem_bytes(c->pad);
-    static size_t smem_set = 0;  // raised only when a larger pad needs it
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
+    // the previous list's rows are stale: every slot back to the sentinel
+    cudaError_t e = fill_list_sentinel(c);
+    if (e != cudaSuccess) return e;
+    switch (c->T) {
+        case 1: e = launch_build_t<1>(c, a); break;
+        case 2: e = launch_build_t<2>(c, a); break;
+        case 4: e = launch_build_t<4>(c, a); break;
+        case 8: e = launch_build_t<8>(c, a); break;
+        default: return cudaErrorInvalidValue;
     }
-    k_build<<<c->ncell_tot, kThreads, smem, c->stream>>>(a);
     c->kernels += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace mdb
