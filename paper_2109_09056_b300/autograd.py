@@ -8,6 +8,13 @@ tables; system: an MDSystem whose types and box define the rest.  F is the
 (n, 3) FP64 force tensor and E the potential energy (0-d tensor).  The
 backward re-bins, re-sorts and rebuilds the neighbor list from the saved
 positions; no list is kept from the forward pass.
+
+Gradient convention for the tables: md_force_backward returns, for an
+unordered type pair {a, b}, the derivative with respect to the one parameter
+both entries hold.  autograd treats eps[a, b] and eps[b, a] as two entries,
+so each off-diagonal entry receives half of it; for any symmetric
+parameterisation (eps = (E + E^T) / 2, a shared scalar, ...) the chain rule
+then gives the exact gradient.
 """
 from __future__ import annotations
 
@@ -17,13 +24,19 @@ import torch
 from .api import MDSystem
 
 
+def _entrywise(g: np.ndarray) -> np.ndarray:
+    out = 0.5 * g
+    np.fill_diagonal(out, np.diag(g))
+    return out
+
+
 class LJForce(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, eps, sigma, system: MDSystem):
         system.set_params(eps.detach().cpu().numpy(), sigma.detach().cpu().numpy())
         system.set_positions(x.detach())
         energy = system.compute_forces()
-        st = system.state(device=x.device)
+        st = system.state(device=x.device if x.is_cuda else None)
         ctx.system = system
         ctx.save_for_backward(x.detach(), eps.detach(), sigma.detach())
         f = st["f"]
@@ -39,8 +52,8 @@ class LJForce(torch.autograd.Function):
         system.set_positions(x)
         gF = torch.zeros_like(x) if gF is None else gF.contiguous().to(torch.float64)
         ge = 0.0 if gE is None else float(gE)
-        dx, de, ds = system.force_backward(gF, ge, device=x.device)
+        dx, de, ds = system.force_backward(gF, ge, device=x.device if x.is_cuda else None)
         if not isinstance(dx, torch.Tensor):
             dx = torch.from_numpy(np.asarray(dx))
-        return (dx.to(x.device), torch.from_numpy(de).to(eps.device),
-                torch.from_numpy(ds).to(sigma.device), None)
+        return (dx.to(x.device), torch.from_numpy(_entrywise(de)).to(eps.device),
+                torch.from_numpy(_entrywise(ds)).to(sigma.device), None)
