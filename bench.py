@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -258,6 +259,32 @@ def run_ours(args, dist):
         out["accuracy"] = {"force_rel_l2_mixed_vs_fp64": rel,
                            "pe_rel_mixed_vs_fp64": abs(pe_m - pe_d) / abs(pe_d)}
         s64.close()
+
+    # ---- batched ensemble: 512 boxes in one context -------------------------
+    if not args.no_batch:
+        ens = mi.ensemble(nbox=512, seed=11)
+        import numpy as np
+        xb = np.concatenate([b.x for b in ens])
+        vb = np.concatenate([b.v for b in ens])
+        tb = np.concatenate([b.types for b in ens])
+        nb = int(sum(b.n for b in ens))
+        sb = MDSystem(xb, vb, tb, None, precision="mixed", n_per_box=[b.n for b in ens],
+                      boxes=[b.box for b in ens], **common)
+        sb.step(MD_PER_STEP)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        kb0 = sb.launch_count()
+        b0.record(stream)
+        sb.step(MD_PER_STEP * args.steps)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        msb = b0.elapsed_time(b1)
+        out["batch"] = {"workload": "lj_ensemble_512", "boxes": len(ens), "atoms": nb,
+                        "value": nb * MD_PER_STEP * args.steps / (msb * 1e-3), "unit": UNIT,
+                        "ms_per_step": msb / args.steps, "precision": "mixed",
+                        "gpu_launches": sb.launch_count() - kb0}
+        sb.close()
 
     # ---- roofline of the dominant kernel -----------------------------------
     t_launch = force_ms / max(n_force, 1) * 1e-3
