@@ -484,7 +484,9 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
 }
 
 template <int T, bool ONE>
-__global__ void __launch_bounds__(128, MD_FORCE_MINB) k_force_mixed(ForceArgs a) {
+// Register budget: MD_FORCE_MINB resident 128-thread CTAs per SM (the same
+// per-thread budget serves 64- and 256-thread CTAs).
+__global__ void __launch_bounds__(256, (MD_FORCE_MINB + 1) / 2) k_force_mixed(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
         if (a.mode == MODE_FUSED) {
             for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(128, MD_FORCE_MINB) k_force_mixed(ForceArgs a)
     }
     extern __shared__ __align__(16) uint32_t lbuf[];
     __shared__ SmemTabs tb;
-    __shared__ __align__(16) float4 s_off[4][32];
+    __shared__ __align__(16) float4 s_off[8][32];
     const Pair &P = *a.pair;
     for (int t = threadIdx.x; t < 64; t += blockDim.x) {
         tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
@@ -704,27 +706,29 @@ __global__ void k_get_neighbors(const Box *__restrict__ boxes, const int32_t *__
 template <bool MIXED, int T, bool ONE>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if (MIXED) {
-        // 4 warps per CTA, each with a double buffer of R list rows.
-        const int block = 128;
-        const size_t smem = (size_t)4 * 2 * a.R * 32 * sizeof(uint32_t);
+        // 2, 4 or 8 warps per CTA, each with a double buffer of R list rows.
+        const int block = c->block;
+        const int warps = block / 32;
+        const size_t smem = (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
         static size_t smem_set = 0, occ_smem = 0;
-        static int occ = 0;
+        static int occ = 0, occ_block = 0;
         if (smem > smem_set) {
             cudaError_t e = cudaFuncSetAttribute(
                 k_force_mixed<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             smem_set = smem;
         }
-        if (occ_smem != smem) {
+        if (occ_smem != smem || occ_block != block) {
             int per = 0;
             cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per, k_force_mixed<T, ONE>, block, smem);
             if (e != cudaSuccess) return e;
             occ = per > 0 ? per : 1;
             occ_smem = smem;
+            occ_block = block;
         }
         int64_t grid = (int64_t)c->nsm * occ;
-        const int64_t need = (a.nwt + 3) / 4;
+        const int64_t need = (a.nwt + warps - 1) / warps;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
