@@ -36,6 +36,9 @@
 #ifndef MD_FORCE_BATCH
 #define MD_FORCE_BATCH 4
 #endif
+#ifndef MD_FORCE_PIPE
+#define MD_FORCE_PIPE 0   // 1: gather the next batch's neighbors while evaluating this one
+#endif
 #ifndef MD_FORCE_MINB
 #define MD_FORCE_MINB 6   // measured best on B300 at 4M atoms (5: 1.03 ms, 6: 0.94 ms)
 #endif

@@ -128,20 +128,24 @@ __device__ __forceinline__ float epilogue(const ForceArgs &a, const SmemTabs &tb
             disp2 += dd * dd;
         }
     } else {
+        // streaming accesses (read or written once per step): keep them out of
+        // L1, which holds the neighbor shadows the gathers reuse
         double vv;
+        const double v0 = __ldcs(a.v + o);
+        const double r0 = __ldcs(a.r_in + o);
         if (THERMO) {
-            const double vh = fma(tb.hdtm[ti], F, a.v[o]);
+            const double vh = fma(tb.hdtm[ti], F, v0);
             ke += 0.5 * tb.mass[ti] * vh * vh;
             p += tb.mass[ti] * vh;
-            const double dd = a.r_in[o] - a.rbuild[o];
+            const double dd = r0 - a.rbuild[o];
             disp2 += dd * dd;
             vv = fma(tb.hdtm[ti], F, vh);
         } else {
-            vv = fma(tb.dtm[ti], F, a.v[o]);
+            vv = fma(tb.dtm[ti], F, v0);
         }
-        a.v[o] = vv;
-        const double rn = fma(a.pair->dt, vv, a.r_in[o]);
-        a.r_out[o] = rn;
+        __stcs(a.v + o, vv);
+        const double rn = fma(a.pair->dt, vv, r0);
+        __stcs(a.r_out + o, rn);
         snew = __double2float_rn(rn);
     }
     return snew;
@@ -322,8 +326,17 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
 // rows as the tile's longest row needs.  Neighbor shadows are gathered
 // kBatch at a time per lane.
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+// The list is read once per step: its copies carry an L2 evict-first policy so
+// they do not push out the neighbor shadows (small enough to stay in L2).
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint64_t pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(saddr),
+                 "l"(g), "l"(pol)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -338,7 +351,8 @@ __device__ __forceinline__ void prefetch_rows(const uint32_t *nbr, int64_t wt, i
                                               uint32_t *dst, int lane) {
     const uint32_t *src = nbr + (size_t)wt * R * 32;
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
-    for (int c = lane; c < rows * 8; c += 32) cp_async16(s + 16u * c, src + 4 * c);
+    const uint64_t pol = l2_evict_first_policy();
+    for (int c = lane; c < rows * 8; c += 32) cp_async16(s + 16u * c, src + 4 * c, pol);
 }
 
 // List rows a warp-tile needs: its longest row, rounded up to whole batches
@@ -402,6 +416,62 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
         // Whole batches up to the tile's row count; entries past this lane's
         // count are sentinels (far dummy), masked like any pair beyond rc.
+        // one list entry: x_j - x_i from the shadows and the stencil offset,
+        // the LJ pair term masked at rc, Kahan-accumulated in list order
+        auto pair = [&](const uint32_t e, const float4 &sj) {
+            const float4 o = s_off[wib][e >> MD_IDX_BITS];
+            const float dx = (sj.x + o.x) - si.x;
+            const float dy = (sj.y + o.y) - si.y;
+            const float dz = (sj.z + o.z) - si.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const bool in = r2 < rc2f;
+            float e24, s2, e4, ush;
+            if (ONE) {
+                e24 = e24_0; s2 = s2_0; e4 = e4_0; ush = ush_0;
+            } else {
+                const int ab = ti * nt + __float_as_int(sj.w);
+                e24 = tb.fe24[ab]; s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
+            }
+            const float r2inv = __fdividef(1.0f, r2);
+            const float q2 = s2 * r2inv;
+            const float s6 = q2 * q2 * q2;
+            const float phi = in ? e24 * r2inv * s6 * fmaf(2.0f, s6, -1.0f) : 0.0f;
+            kahan_add(fx, cx, -phi * dx);
+            kahan_add(fy, cy, -phi * dy);
+            kahan_add(fz, cz, -phi * dz);
+            if (THERMO) kahan_add(pe, cp, in ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f);
+        };
+#if MD_FORCE_PIPE
+        // gathers of the next batch are in flight while this batch is evaluated
+        uint32_t e[kBatch];
+        float4 sj[kBatch];
+        if (rows_cur > 0) {
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = Lr[u * 32];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (e[u] & MD_IDX_MASK));
+        }
+        for (int q0 = 0; q0 < rows_cur; q0 += kBatch) {
+            const bool more = q0 + kBatch < rows_cur;
+            uint32_t en[kBatch];
+            float4 sn[kBatch];
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) en[u] = Lr[(q0 + kBatch + u) * 32];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) sn[u] = __ldg(a.sh_in + (en[u] & MD_IDX_MASK));
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) pair(e[u], sj[u]);
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    e[u] = en[u];
+                    sj[u] = sn[u];
+                }
+            }
+        }
+#else
         for (int q0 = 0; q0 < rows_cur; q0 += kBatch) {
             uint32_t e[kBatch];
 #pragma unroll
@@ -410,30 +480,9 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (e[u] & MD_IDX_MASK));
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const float4 o = s_off[wib][e[u] >> MD_IDX_BITS];
-                const float dx = (sj[u].x + o.x) - si.x;
-                const float dy = (sj[u].y + o.y) - si.y;
-                const float dz = (sj[u].z + o.z) - si.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const bool in = r2 < rc2f;
-                float e24, s2, e4, ush;
-                if (ONE) {
-                    e24 = e24_0; s2 = s2_0; e4 = e4_0; ush = ush_0;
-                } else {
-                    const int ab = ti * nt + __float_as_int(sj[u].w);
-                    e24 = tb.fe24[ab]; s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
-                }
-                const float r2inv = __fdividef(1.0f, r2);
-                const float q2 = s2 * r2inv;
-                const float s6 = q2 * q2 * q2;
-                const float phi = in ? e24 * r2inv * s6 * fmaf(2.0f, s6, -1.0f) : 0.0f;
-                kahan_add(fx, cx, -phi * dx);
-                kahan_add(fy, cy, -phi * dy);
-                kahan_add(fz, cz, -phi * dz);
-                if (THERMO) kahan_add(pe, cp, in ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f);
-            }
+            for (int u = 0; u < kBatch; ++u) pair(e[u], sj[u]);
         }
+#endif
         __syncwarp();  // done reading buf[cb]; the next prefetch may refill it
         merge_lanes<T>(fx, cx);
         merge_lanes<T>(fy, cy);

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
         const float4 si = a.sh[i];
         int cnt = 0;
         // this lane's row: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
-        uint32_t *rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
+        uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
+        uint32_t *wp = rowp;  // where entry cnt goes
         for (int w0 = 0; w0 < M; w0 += kCand) {
             const int Mw = min(kCand, M - w0);
             __syncwarp();
@@ -132,39 +133,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
             __syncwarp();
             if (active) {
                 const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
-                // accept candidate p (already known to be within the band's top)
-                auto take = [&](const float4 &p, float dx, float dy, float dz, float r2) {
-                    const uint32_t meta = __float_as_uint(p.w);
-                    const int64_t j = meta & MD_IDX_MASK;
-                    bool acc = j != i;
-                    if (acc && r2 >= lo) acc = exact_test(a, B, i, j, dx, dy, dz);
-                    if (acc) {
-                        if (cnt < a.pad) rowp[(cnt / T) * 32 + (cnt % T)] = meta;
-                        ++cnt;
-                    }
-                };
-                int k = 0;
-                // four independent distance tests per step, appended in order
-                for (; k + 4 <= Mw; k += 4) {
-                    float4 p[4];
-                    float dx[4], dy[4], dz[4], r2[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        p[u] = cand[w][k + u];
-                        dx[u] = p[u].x - si.x;
-                        dy[u] = p[u].y - si.y;
-                        dz[u] = p[u].z - si.z;
-                        r2[u] = fmaf(dx[u], dx[u], fmaf(dy[u], dy[u], dz[u] * dz[u]));
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (r2[u] <= hi) take(p[u], dx[u], dy[u], dz[u], r2[u]);
-                }
-                for (; k < Mw; ++k) {
+                const uint32_t self = (uint32_t)i;
+#pragma unroll 4
+                for (int k = 0; k < Mw; ++k) {
                     const float4 p = cand[w][k];
                     const float dx = p.x - si.x, dy = p.y - si.y, dz = p.z - si.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if (r2 <= hi) take(p, dx, dy, dz, r2);
+                    if (r2 <= hi) {
+                        const uint32_t meta = __float_as_uint(p.w);
+                        bool acc = (meta & MD_IDX_MASK) != self;
+                        if (acc && r2 >= lo)   // rare: the exact FP64 decision
+                            acc = exact_test(a, B, i, meta & MD_IDX_MASK, dx, dy, dz);
+                        if (acc) {
+                            if (cnt < a.pad) *wp = meta;
+                            // next slot of the row: +1 within a group of T, else the next row
+                            wp += (cnt % T == T - 1) ? (33 - T) : 1;
+                            ++cnt;
+                        }
+                    }
                 }
             }
         }
