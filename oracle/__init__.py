@@ -50,8 +50,12 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = C.CDLL(_LIB)
+            # ORACLE_LIB: an alternative build of oracle_md.c (the mutation
+            # test loads deliberately broken copies to check the pins catch them)
+            alt = os.environ.get("ORACLE_LIB")
+            if not alt:
+                build()
+            lib = C.CDLL(alt or _LIB)
             P = C.c_void_p
             i64, i32, dbl = C.c_int64, C.c_int32, C.c_double
             sig = {

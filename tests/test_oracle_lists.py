@@ -57,6 +57,20 @@ def test_cell_index_contains_atom(orc):
     assert np.all(x >= c * h - 1e-12) and np.all(x <= (c + 1) * h + 1e-12)
 
 
+def test_cell_linear_order(orc):
+    """c = (cz * nc_y + cy) * nc_x + cx, x fastest, on a box with distinct nc per axis."""
+    L = np.array([12.0, 15.0, 18.0])
+    nc = orc.cell_grid(L, 2.8)
+    assert list(nc) == [4, 5, 6]
+    h = L / nc
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        c = rng.integers(0, nc)
+        x = (c + rng.uniform(0.1, 0.9, 3)) * h
+        cell = orc.cell_index(x[None, :], L, nc)[0]
+        assert cell == (c[2] * nc[1] + c[1]) * nc[0] + c[0]
+
+
 def test_stable_sort_equals_library_sort(orc):
     rng = np.random.default_rng(3)
     for ncell, n in [(5, 1000), (125, 4000), (6859, 50000), (1, 7)]:

@@ -70,6 +70,12 @@ def test_eps_sigma_scaling_law(orc):
 def test_cutoff_strict_and_shift(orc):
     f, pe = dimer(orc, 2.5)                    # r^2 == rc^2 exactly: no interaction
     assert pe == 0.0 and np.all(f == 0.0)
+    # the same through the neighbor-list path (the pair is inside rc + skin)
+    x = np.array([[10.0, 10.0, 10.0], [12.5, 10.0, 10.0]])
+    fl, _, pel = orc.lj_forces(x, [0, 0], BIG)
+    assert pel == 0.0 and np.all(fl == 0.0)
+    x[1, 0] = 12.5 - 1e-9
+    assert orc.lj_forces(x, [0, 0], BIG)[2] < 0
     f, pe = dimer(orc, 2.5 - 1e-9)
     assert pe < 0 and f[1, 0] < 0               # attractive just inside
     _, pes = dimer(orc, 2.5 - 1e-9, shift=True)  # shifted: continuous at rc
