@@ -137,6 +137,7 @@ md_status setup_pair(md_ctx *c, const double *eps, const double *sigma) {
             P.fs2[ab] = (float)P.s2[ab];
             P.fe4[ab] = (float)P.e4[ab];
             P.fush[ab] = (float)P.ush[ab];
+            P.fc1[ab] = (float)(P.e24[ab] / P.s2[ab]);
         }
     for (int a = 0; a < nt; ++a) {
         P.mass[a] = c->mass[a];

@@ -36,11 +36,27 @@
 #ifndef MD_FORCE_BATCH
 #define MD_FORCE_BATCH 4
 #endif
-#ifndef MD_FORCE_PIPE
-#define MD_FORCE_PIPE 0   // 1: gather the next batch's neighbors while evaluating this one
-#endif
 #ifndef MD_FORCE_MINB
 #define MD_FORCE_MINB 6   // measured best on B300 at 4M atoms (5: 1.03 ms, 6: 0.94 ms)
+#endif
+// List rows: 1 = loaded into registers one batch ahead; 0 = a whole tile's rows
+// staged in a shared-memory double buffer with cp.async.
+#ifndef MD_FORCE_LIST
+#define MD_FORCE_LIST 1
+#endif
+// Terms combined by an FMA chain before each Kahan add (1, 2 or 4).
+#ifndef MD_FORCE_KSUM
+#define MD_FORCE_KSUM 1
+#endif
+// 1: rows past the last whole batch are evaluated one at a time instead of
+// rounding a tile's row count up to a whole batch.
+#ifndef MD_FORCE_TAIL
+#define MD_FORCE_TAIL 1
+#endif
+// Merge of an atom's T lane sums: 0 = TwoSum on (sum, compensation) pairs;
+// 1 = each lane folds its compensation, then a plain xor-shuffle sum.
+#ifndef MD_FORCE_MERGE
+#define MD_FORCE_MERGE 0
 #endif
 
 namespace mdb {
@@ -79,6 +95,7 @@ struct Pair {
     double eps[64], sig[64];
     double e24[64], s2[64], e4[64], ush[64];  // 24 eps, sigma^2, 4 eps, U(rc) (0 if unshifted)
     float fe24[64], fs2[64], fe4[64], fush[64];
+    float fc1[64];  // 24 eps / sigma^2
     double mass[MD_MAXT], dtm[MD_MAXT], hdtm[MD_MAXT];
 };
 

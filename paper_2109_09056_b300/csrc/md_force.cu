@@ -96,7 +96,7 @@ __device__ __forceinline__ double warp_max_d(double x) {
 
 // Shared per-CTA tables.
 struct SmemTabs {
-    float fe24[64], fs2[64], fe4[64], fush[64];
+    float fe24[64], fs2[64], fe4[64], fush[64], fc1[64];
     double de24[64], ds2[64], de4[64], dush[64];
     double dtm[MD_MAXT], hdtm[MD_MAXT], mass[MD_MAXT];
 };
@@ -317,21 +317,29 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
     }
 }
 
-// ---- mixed-precision kernel with the list streamed through shared memory ----
+// ---- mixed-precision kernel ----
 //
 // Each warp walks a contiguous run of warp-tiles (the CTA's chunk, warps
-// interleaved, so the CTA's warps share neighbors in L1).  While it evaluates
-// tile t it has its next tile's list rows in flight: cp.async (16-byte,
-// L1-bypassing) copies into a per-warp double buffer, only as many 128-byte
-// rows as the tile's longest row needs.  Neighbor shadows are gathered
-// kBatch at a time per lane.
+// interleaved, so the CTA's warps share neighbors in L1).  List rows are read
+// one batch ahead of their use, so only the neighbor gathers wait on memory:
+// with MD_FORCE_LIST 1 straight into registers (the batch after the current
+// one; at a tile's end, the next tile's first batch), with MD_FORCE_LIST 0 a
+// whole tile's rows at a time into a per-warp shared-memory double buffer
+// (cp.async).  Neighbor shadows are gathered kBatch at a time per lane.
 
-// The list is read once per step: its copies carry an L2 evict-first policy so
+// The list is read once per step: its loads carry an L2 evict-first policy so
 // they do not push out the neighbor shadows (small enough to stay in L2).
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
     return pol;
+}
+__device__ __forceinline__ uint32_t ld_list(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;\n"
+        : "=r"(v)
+        : "l"(p), "l"(pol));
+    return v;
 }
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint64_t pol) {
     asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(saddr),
@@ -355,18 +363,28 @@ __device__ __forceinline__ void prefetch_rows(const uint32_t *nbr, int64_t wt, i
     for (int c = lane; c < rows * 8; c += 32) cp_async16(s + 16u * c, src + 4 * c, pol);
 }
 
-// List rows a warp-tile needs: its longest row, rounded up to whole batches
-// (rows past an atom's count hold the sentinel entry).
+// List rows a warp-tile needs: its longest row (rows past an atom's count hold
+// the sentinel entry), rounded up to whole batches unless the rows past the
+// last whole batch are evaluated one at a time.
 template <int T>
 __device__ __forceinline__ int tile_rows(int ni) {
     const int r = __reduce_max_sync(0xffffffffu, (ni + T - 1) / T);
-    return (r + kBatch - 1) / kBatch * kBatch;
+    return MD_FORCE_TAIL ? r : (r + kBatch - 1) / kBatch * kBatch;
+}
+
+template <int T>
+__device__ __forceinline__ float sum_lanes_f(float x) {
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
 template <int T, bool ONE, bool THERMO>
 __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
                                            float4 (*s_off)[32], uint32_t *lbuf) {
     constexpr int A = 32 / T;
+    constexpr int G = MD_FORCE_KSUM;
+    static_assert(kBatch % G == 0, "MD_FORCE_KSUM must divide MD_FORCE_BATCH");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, sub = lane % T;
     const int nwc = blockDim.x >> 5;
     const int64_t chunk = (a.nwt + gridDim.x - 1) / gridDim.x;
@@ -374,10 +392,23 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     const int64_t t1 = min(a.nwt, t0 + chunk);
     const int nt = a.pair->nt;
     const float rc2f = a.pair->rc2f;
-    const float e24_0 = tb.fe24[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
-    uint32_t *const buf0 = lbuf + (size_t)wib * 2 * a.R * 32;
-    const int bstride = a.R * 32;
+    const float c1_0 = tb.fc1[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
+    const float c1x2_0 = 2.0f * c1_0;
+    const size_t rowblk = (size_t)a.R * 32;  // words in one warp-tile's list block
     int64_t wt = t0 + wib;
+#if MD_FORCE_LIST
+    (void)lbuf;
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t e[kBatch];  // the next batch of this lane's entries, already loaded
+    int nn_cur = 0;
+    if (wt < t1) {
+        nn_cur = __ldg(a.nn + wt * A + lane / T);
+        const uint32_t *L0 = a.nbr + wt * rowblk + lane;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) e[u] = ld_list(L0 + u * 32, pol);
+    }
+#else
+    uint32_t *const buf0 = lbuf + (size_t)wib * 2 * rowblk;
     int rows_cur = 0;
     if (wt < t1) {
         rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
@@ -385,15 +416,24 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     }
     cp_async_commit();
     int cb = 0;
+#endif
     int curbox = -1;
     for (; wt < t1; wt += nwc) {
         const int64_t wn = wt + nwc;
+        const bool has_next = wn < t1;
+#if MD_FORCE_LIST
+        const int nn_next = has_next ? __ldg(a.nn + wn * A + lane / T) : 0;
+        const int rows_cur = tile_rows<T>(min(nn_cur, a.pad));
+        const uint32_t *Lc = a.nbr + wt * rowblk + lane;
+        const uint32_t *Ln = a.nbr + wn * rowblk + lane;  // read only if has_next
+#else
         int rows_next = 0;
-        if (wn < t1) {
+        if (has_next) {
             rows_next = tile_rows<T>(min(__ldg(a.nn + wn * A + lane / T), a.pad));
-            prefetch_rows(a.nbr, wn, a.R, rows_next, buf0 + (cb ^ 1) * bstride, lane);
+            prefetch_rows(a.nbr, wn, a.R, rows_next, buf0 + (cb ^ 1) * rowblk, lane);
         }
         cp_async_commit();
+#endif
         const int64_t i = wt * A + lane / T;
         const int b = a.tile_box[(wt * A) >> 5];
         const Box &B = a.boxes[b];
@@ -410,88 +450,134 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         const bool valid = (i - B.slot_off) < B.n;
         const float4 si = a.sh_in[i];
         const int ti = ONE ? 0 : __float_as_int(si.w);
+#if MD_FORCE_LIST
+        __syncwarp();  // s_off is visible to the whole warp
+#else
         cp_async_wait<1>();  // this lane's copies of the current tile have landed
         __syncwarp();        // ... and every other lane's; s_off is visible too
-        const uint32_t *Lr = buf0 + cb * bstride + lane;
+        const uint32_t *Lr = buf0 + cb * rowblk + lane;
+#endif
         float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
-        // Whole batches up to the tile's row count; entries past this lane's
-        // count are sentinels (far dummy), masked like any pair beyond rc.
-        // one list entry: x_j - x_i from the shadows and the stencil offset,
-        // the LJ pair term masked at rc, Kahan-accumulated in list order
-        auto pair = [&](const uint32_t e, const float4 &sj) {
-            const float4 o = s_off[wib][e >> MD_IDX_BITS];
+        // One list entry: x_j - x_i from the shadows and the stencil offset,
+        // the LJ term masked at rc (sentinel entries past an atom's count sit
+        // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
+        auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
+                         float &tp) {
+            const float4 o = s_off[wib][en >> MD_IDX_BITS];
             const float dx = (sj.x + o.x) - si.x;
             const float dy = (sj.y + o.y) - si.y;
             const float dz = (sj.z + o.z) - si.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const bool in = r2 < rc2f;
-            float e24, s2, e4, ush;
+            float s2, e4, ush, w;
+            const float r2inv = __fdividef(1.0f, r2);
             if (ONE) {
-                e24 = e24_0; s2 = s2_0; e4 = e4_0; ush = ush_0;
+                s2 = s2_0; e4 = e4_0; ush = ush_0;
             } else {
                 const int ab = ti * nt + __float_as_int(sj.w);
-                e24 = tb.fe24[ab]; s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
+                s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
             }
-            const float r2inv = __fdividef(1.0f, r2);
             const float q2 = s2 * r2inv;
             const float s6 = q2 * q2 * q2;
-            const float phi = in ? e24 * r2inv * s6 * fmaf(2.0f, s6, -1.0f) : 0.0f;
-            kahan_add(fx, cx, -phi * dx);
-            kahan_add(fy, cy, -phi * dy);
-            kahan_add(fz, cz, -phi * dz);
-            if (THERMO) kahan_add(pe, cp, in ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f);
-        };
-#if MD_FORCE_PIPE
-        // gathers of the next batch are in flight while this batch is evaluated
-        uint32_t e[kBatch];
-        float4 sj[kBatch];
-        if (rows_cur > 0) {
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) e[u] = Lr[u * 32];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (e[u] & MD_IDX_MASK));
-        }
-        for (int q0 = 0; q0 < rows_cur; q0 += kBatch) {
-            const bool more = q0 + kBatch < rows_cur;
-            uint32_t en[kBatch];
-            float4 sn[kBatch];
-            if (more) {
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) en[u] = Lr[(q0 + kBatch + u) * 32];
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) sn[u] = __ldg(a.sh_in + (en[u] & MD_IDX_MASK));
+            // phi = 24 eps / r^2 (sigma/r)^6 [2 (sigma/r)^6 - 1] = c1 q2 s6 (2 s6 - 1)
+            if (ONE) {
+                w = fmaf(c1x2_0, s6, -c1_0);
+            } else {
+                w = tb.fc1[ti * nt + __float_as_int(sj.w)] * fmaf(2.0f, s6, -1.0f);
             }
+            const float phi = in ? (q2 * s6) * w : 0.0f;
+            tx = -phi * dx;
+            ty = -phi * dy;
+            tz = -phi * dz;
+            tp = (THERMO && in) ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f;
+        };
+        // groups of G consecutive terms are added by an FMA chain, each group
+        // sum by one Kahan step
+        auto batch = [&](const uint32_t (&eb)[kBatch], const float4 (&sj)[kBatch]) {
+            float gx = 0.f, gy = 0.f, gz = 0.f, gp = 0.f;
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) pair(e[u], sj[u]);
-            if (more) {
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    e[u] = en[u];
-                    sj[u] = sn[u];
+            for (int u = 0; u < kBatch; ++u) {
+                float tx, ty, tz, tp;
+                terms(eb[u], sj[u], tx, ty, tz, tp);
+                if (u % G == 0) {
+                    gx = tx; gy = ty; gz = tz; gp = tp;
+                } else {
+                    gx += tx; gy += ty; gz += tz; gp += tp;
+                }
+                if (u % G == G - 1) {
+                    kahan_add(fx, cx, gx);
+                    kahan_add(fy, cy, gy);
+                    kahan_add(fz, cz, gz);
+                    if (THERMO) kahan_add(pe, cp, gp);
                 }
             }
-        }
-#else
-        for (int q0 = 0; q0 < rows_cur; q0 += kBatch) {
-            uint32_t e[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) e[u] = Lr[(q0 + u) * 32];
+        };
+        auto single = [&](const uint32_t en) {
+            const float4 sj = __ldg(a.sh_in + (en & MD_IDX_MASK));
+            float tx, ty, tz, tp;
+            terms(en, sj, tx, ty, tz, tp);
+            kahan_add(fx, cx, tx);
+            kahan_add(fy, cy, ty);
+            kahan_add(fz, cz, tz);
+            if (THERMO) kahan_add(pe, cp, tp);
+        };
+        const int rows_full = rows_cur / kBatch * kBatch;  // == rows_cur unless MD_FORCE_TAIL
+#if MD_FORCE_LIST
+        for (int q = 0; q < rows_full; q += kBatch) {
             float4 sj[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (e[u] & MD_IDX_MASK));
+            // the batch after this one: this tile's next rows, else the next tile's first
+            const bool more = q + kBatch < rows_full;
+            uint32_t en[kBatch];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) pair(e[u], sj[u]);
+            for (int u = 0; u < kBatch; ++u) en[u] = e[u];
+            if (more || has_next) {
+                const uint32_t *P = more ? Lc + (size_t)(q + kBatch) * 32 : Ln;
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) en[u] = ld_list(P + u * 32, pol);
+            }
+            batch(e, sj);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = en[u];
         }
-#endif
+        if (rows_full == 0 && has_next) {
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) e[u] = ld_list(Ln + u * 32, pol);
+        }
+        for (int q = rows_full; q < rows_cur; ++q) single(ld_list(Lc + (size_t)q * 32, pol));
+#else
+        for (int q = 0; q < rows_full; q += kBatch) {
+            uint32_t eb[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) eb[u] = Lr[(q + u) * 32];
+            float4 sj[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (eb[u] & MD_IDX_MASK));
+            batch(eb, sj);
+        }
+        for (int q = rows_full; q < rows_cur; ++q) single(Lr[q * 32]);
         __syncwarp();  // done reading buf[cb]; the next prefetch may refill it
+#endif
+#if MD_FORCE_MERGE
+        fx = sum_lanes_f<T>(fx - cx);
+        fy = sum_lanes_f<T>(fy - cy);
+        fz = sum_lanes_f<T>(fz - cz);
+        double ped = 0.0;
+        if (THERMO) ped = (double)sum_lanes_f<T>(pe - cp);
+#else
         merge_lanes<T>(fx, cx);
         merge_lanes<T>(fy, cy);
         merge_lanes<T>(fz, cz);
+        fx -= cx;
+        fy -= cy;
+        fz -= cz;
         double ped = 0.0;
         if (THERMO) {
             merge_lanes<T>(pe, cp);
-            ped = (double)pe;
+            ped = (double)(pe - cp);
         }
+#endif
         // Epilogue: one FP64 update per component, the components spread over
         // the atom's lanes (lane sub takes components sub, sub + T, ...).
         double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
@@ -526,10 +612,16 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
                 tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
             }
         }
+#if MD_FORCE_LIST
+        nn_cur = nn_next;
+#else
         cb ^= 1;
         rows_cur = rows_next;
+#endif
     }
+#if !MD_FORCE_LIST
     cp_async_wait<0>();
+#endif
 }
 
 template <int T, bool ONE>
@@ -552,6 +644,7 @@ __global__ void __launch_bounds__(256, (MD_FORCE_MINB + 1) / 2) k_force_mixed(Fo
     const Pair &P = *a.pair;
     for (int t = threadIdx.x; t < 64; t += blockDim.x) {
         tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
+        tb.fc1[t] = P.fc1[t];
         if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
     }
     __syncthreads();
@@ -591,6 +684,7 @@ __global__ void __launch_bounds__(256, 2) k_force(ForceArgs a) {
     const Pair &P = *a.pair;
     for (int t = threadIdx.x; t < 64; t += blockDim.x) {
         tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
+        tb.fc1[t] = P.fc1[t];
         tb.de24[t] = P.e24[t]; tb.ds2[t] = P.s2[t]; tb.de4[t] = P.e4[t]; tb.dush[t] = P.ush[t];
         if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
     }
@@ -758,7 +852,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         // 2, 4 or 8 warps per CTA, each with a double buffer of R list rows.
         const int block = c->block;
         const int warps = block / 32;
-        const size_t smem = (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
+        const size_t smem = MD_FORCE_LIST ? 0 : (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
         static size_t smem_set = 0, occ_smem = 0;
         static int occ = 0, occ_block = 0;
         if (smem > smem_set) {
