@@ -25,6 +25,10 @@ md_status fail(md_ctx *c, md_status s, const std::string &msg) {
     return s;
 }
 
+md_status timeout_fail(md_ctx *c) {
+    return fail(c, MD_ERR_TIMEOUT, "a bounded device wait expired (a list copy did not complete)");
+}
+
 md_status cuda_fail(md_ctx *c, cudaError_t e, const char *where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     return fail(c, e == cudaErrorMemoryAllocation ? MD_ERR_NOMEM : MD_ERR_CUDA, m);
@@ -206,6 +210,7 @@ md_status sort_build_forces(md_ctx *c, bool raw) {
     CK(launch_finalize(c, MODE_FORCE_ONLY));
     s = read_flags(c);
     if (s) return s;
+    if (c->hflags->status & ST_TIMEOUT) return timeout_fail(c);
     if (c->hflags->status & ST_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position");
     c->forces_valid = true;
     c->ready = true;
@@ -504,6 +509,7 @@ md_status md_bin_sort(md_ctx *c) {
     CK(launch_bin_sort(c, false));
     md_status s = read_flags(c);
     if (s) return s;
+    if (c->hflags->status & ST_TIMEOUT) return timeout_fail(c);
     if (c->hflags->status & ST_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position");
     c->sorted = true;
     c->built_at = -1;
@@ -679,6 +685,7 @@ md_status md_step(md_ctx *c, int32_t nsteps, md_thermo *last_out) {
             if (s) return s;
         }
         const uint32_t st = c->hflags->status;
+        if (st & ST_TIMEOUT) return timeout_fail(c);
         if (st & ST_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position during md_step");
         if (!(st & ST_OVERFLOW)) {
             c->step = target;

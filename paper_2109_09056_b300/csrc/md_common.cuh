@@ -40,7 +40,8 @@
 #define MD_FORCE_MINB 6   // measured best on B300 at 4M atoms (5: 1.03 ms, 6: 0.94 ms)
 #endif
 // List rows: 1 = loaded into registers one batch ahead; 0 = a whole tile's rows
-// staged in a shared-memory double buffer with cp.async.
+// staged in a shared-memory double buffer with cp.async; 2 = the same buffer
+// filled by one bulk (TMA) copy per tile.
 #ifndef MD_FORCE_LIST
 #define MD_FORCE_LIST 1
 #endif
@@ -53,6 +54,11 @@
 #ifndef MD_FORCE_TAIL
 #define MD_FORCE_TAIL 1
 #endif
+// Stencil offset of a list entry: 0 = a 27-entry float4 table in shared
+// memory; 1 = three warp shuffles from the lanes holding the table.
+#ifndef MD_FORCE_OFFSET
+#define MD_FORCE_OFFSET 0
+#endif
 // Merge of an atom's T lane sums: 0 = TwoSum on (sum, compensation) pairs;
 // 1 = each lane folds its compensation, then a plain xor-shuffle sum.
 #ifndef MD_FORCE_MERGE
@@ -61,8 +67,8 @@
 
 namespace mdb {
 
-enum : uint32_t { ST_OVERFLOW = 1u, ST_NONFINITE = 2u };
-constexpr uint32_t ST_FREEZE = ST_OVERFLOW | ST_NONFINITE;
+enum : uint32_t { ST_OVERFLOW = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
+constexpr uint32_t ST_FREEZE = ST_OVERFLOW | ST_NONFINITE | ST_TIMEOUT;
 
 // Force-kernel modes.
 enum { MODE_FORCE_ONLY = 0, MODE_FINAL = 1, MODE_FUSED = 2 };

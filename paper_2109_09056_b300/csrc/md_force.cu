@@ -354,6 +354,54 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// MD_FORCE_LIST 2: a tile's rows as one bulk (TMA) copy completing on an mbarrier.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// rows [0, rows) of a list block (128 bytes each) -> shared dst; lane 0 only
+__device__ __forceinline__ void bulk_rows(uint32_t dst, const uint32_t *src, int rows, uint32_t bar,
+                                          uint64_t pol) {
+    const uint32_t bytes = (uint32_t)rows * 128u;
+    // the warp's earlier generic reads of dst come before the async-proxy write
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    if (bytes > 0)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+            "[%0], [%1], %2, [%3], %4;\n" ::"r"(dst),
+            "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+            : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity to complete; false after ~1 s.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t k = 1; k < (1u << 28); ++k) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((k & 255u) == 0u && globaltimer_ns() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+
 // Rows [0, rows) of warp-tile wt's list block -> dst (rows * 32 words).
 __device__ __forceinline__ void prefetch_rows(const uint32_t *nbr, int64_t wt, int R, int rows,
                                               uint32_t *dst, int lane) {
@@ -381,7 +429,8 @@ __device__ __forceinline__ float sum_lanes_f(float x) {
 
 template <int T, bool ONE, bool THERMO>
 __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
-                                           float4 (*s_off)[32], uint32_t *lbuf) {
+                                           float4 (*s_off)[32], uint64_t (*s_bar)[2],
+                                           uint32_t *lbuf) {
     constexpr int A = 32 / T;
     constexpr int G = MD_FORCE_KSUM;
     static_assert(kBatch % G == 0, "MD_FORCE_KSUM must divide MD_FORCE_BATCH");
@@ -396,7 +445,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     const float c1x2_0 = 2.0f * c1_0;
     const size_t rowblk = (size_t)a.R * 32;  // words in one warp-tile's list block
     int64_t wt = t0 + wib;
-#if MD_FORCE_LIST
+#if MD_FORCE_LIST == 1
     (void)lbuf;
     const uint64_t pol = l2_evict_first_policy();
     uint32_t e[kBatch];  // the next batch of this lane's entries, already loaded
@@ -410,18 +459,36 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
 #else
     uint32_t *const buf0 = lbuf + (size_t)wib * 2 * rowblk;
     int rows_cur = 0;
+#if MD_FORCE_LIST == 2
+    const uint64_t pol = l2_evict_first_policy();
+    const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(buf0);
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[wib][0]);
+    uint32_t phase = 0;  // bit k: parity of buffer k's next completion
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (wt < t1) {
+        rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
+        if (lane == 0) bulk_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, bar0, pol);
+    }
+#else
     if (wt < t1) {
         rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
         prefetch_rows(a.nbr, wt, a.R, rows_cur, buf0, lane);
     }
     cp_async_commit();
+#endif
     int cb = 0;
 #endif
     int curbox = -1;
+    float ofx = 0.f, ofy = 0.f, ofz = 0.f;  // MD_FORCE_OFFSET 1: lane k holds code k's offset
     for (; wt < t1; wt += nwc) {
         const int64_t wn = wt + nwc;
         const bool has_next = wn < t1;
-#if MD_FORCE_LIST
+#if MD_FORCE_LIST == 1
         const int nn_next = has_next ? __ldg(a.nn + wn * A + lane / T) : 0;
         const int rows_cur = tile_rows<T>(min(nn_cur, a.pad));
         const uint32_t *Lc = a.nbr + wt * rowblk + lane;
@@ -430,30 +497,53 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         int rows_next = 0;
         if (has_next) {
             rows_next = tile_rows<T>(min(__ldg(a.nn + wn * A + lane / T), a.pad));
+#if MD_FORCE_LIST == 2
+            if (lane == 0)
+                bulk_rows(sbuf0 + (uint32_t)((cb ^ 1) * rowblk * 4), a.nbr + wn * rowblk, rows_next,
+                          bar0 + 8 * (cb ^ 1), pol);
+#else
             prefetch_rows(a.nbr, wn, a.R, rows_next, buf0 + (cb ^ 1) * rowblk, lane);
+#endif
         }
+#if MD_FORCE_LIST == 0
         cp_async_commit();
+#endif
 #endif
         const int64_t i = wt * A + lane / T;
         const int b = a.tile_box[(wt * A) >> 5];
         const Box &B = a.boxes[b];
         if (b != curbox) {
-            if (lane >= 27) {
-                s_off[wib][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
+            // stencil offset of code `lane` (codes 27..31 unused: zero)
+            float4 ol = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane < 27) {
                 const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-                s_off[wib][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
-                                               (float)oz * B.hf[2], 0.f);
+                ol = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1], (float)oz * B.hf[2], 0.f);
             }
+#if MD_FORCE_OFFSET
+            ofx = ol.x; ofy = ol.y; ofz = ol.z;
+#else
+            s_off[wib][lane] = ol;
+#endif
             curbox = b;
         }
         const bool valid = (i - B.slot_off) < B.n;
         const float4 si = a.sh_in[i];
         const int ti = ONE ? 0 : __float_as_int(si.w);
-#if MD_FORCE_LIST
+#if MD_FORCE_LIST == 1
         __syncwarp();  // s_off is visible to the whole warp
 #else
+#if MD_FORCE_LIST == 2
+        // the current tile's rows have landed (bounded wait: on expiry the
+        // step is abandoned with a timeout status)
+        if (!mbar_wait(bar0 + 8 * cb, (phase >> cb) & 1u)) {
+            atomicOr(&a.fl->status, ST_TIMEOUT);
+            if (has_next) mbar_wait(bar0 + 8 * (cb ^ 1), (phase >> (cb ^ 1)) & 1u);
+            return;
+        }
+        phase ^= 1u << cb;
+#else
         cp_async_wait<1>();  // this lane's copies of the current tile have landed
+#endif
         __syncwarp();        // ... and every other lane's; s_off is visible too
         const uint32_t *Lr = buf0 + cb * rowblk + lane;
 #endif
@@ -463,7 +553,15 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
         auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
                          float &tp) {
+#if MD_FORCE_OFFSET
+            const int code = (int)(en >> MD_IDX_BITS);
+            float4 o;
+            o.x = __shfl_sync(0xffffffffu, ofx, code);
+            o.y = __shfl_sync(0xffffffffu, ofy, code);
+            o.z = __shfl_sync(0xffffffffu, ofz, code);
+#else
             const float4 o = s_off[wib][en >> MD_IDX_BITS];
+#endif
             const float dx = (sj.x + o.x) - si.x;
             const float dy = (sj.y + o.y) - si.y;
             const float dz = (sj.z + o.z) - si.z;
@@ -522,7 +620,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             if (THERMO) kahan_add(pe, cp, tp);
         };
         const int rows_full = rows_cur / kBatch * kBatch;  // == rows_cur unless MD_FORCE_TAIL
-#if MD_FORCE_LIST
+#if MD_FORCE_LIST == 1
         for (int q = 0; q < rows_full; q += kBatch) {
             float4 sj[kBatch];
 #pragma unroll
@@ -612,14 +710,14 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
                 tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
             }
         }
-#if MD_FORCE_LIST
+#if MD_FORCE_LIST == 1
         nn_cur = nn_next;
 #else
         cb ^= 1;
         rows_cur = rows_next;
 #endif
     }
-#if !MD_FORCE_LIST
+#if MD_FORCE_LIST == 0
     cp_async_wait<0>();
 #endif
 }
@@ -638,9 +736,10 @@ __global__ void __launch_bounds__(256, (MD_FORCE_MINB + 1) / 2) k_force_mixed(Fo
         }
         return;
     }
-    extern __shared__ __align__(16) uint32_t lbuf[];
+    extern __shared__ __align__(128) uint32_t lbuf[];
     __shared__ SmemTabs tb;
     __shared__ __align__(16) float4 s_off[8][32];
+    __shared__ __align__(8) uint64_t s_bar[8][2];
     const Pair &P = *a.pair;
     for (int t = threadIdx.x; t < 64; t += blockDim.x) {
         tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
@@ -650,8 +749,8 @@ __global__ void __launch_bounds__(256, (MD_FORCE_MINB + 1) / 2) k_force_mixed(Fo
     __syncthreads();
     const int64_t clock = a.fl->clock;
     const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
-    if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, lbuf);
-    else mixed_body<T, ONE, false>(a, tb, s_off, lbuf);
+    if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, s_bar, lbuf);
+    else mixed_body<T, ONE, false>(a, tb, s_off, s_bar, lbuf);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -852,7 +951,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         // 2, 4 or 8 warps per CTA, each with a double buffer of R list rows.
         const int block = c->block;
         const int warps = block / 32;
-        const size_t smem = MD_FORCE_LIST ? 0 : (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
+        const size_t smem = MD_FORCE_LIST == 1 ? 0 : (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
         static size_t smem_set = 0, occ_smem = 0;
         static int occ = 0, occ_block = 0;
         if (smem > smem_set) {
