@@ -47,7 +47,9 @@ typedef enum {
     MD_ERR_DANGEROUS_BUILD = 4,  /* only with md_params.check_displacement: some atom moved
                                     more than skin/2 between two builds; the run completed */
     MD_ERR_NONFINITE = 5,        /* a position or velocity is NaN/Inf; the run froze there */
-    MD_ERR_TIMEOUT = 6,          /* reserved: no library kernel spin-waits */
+    MD_ERR_TIMEOUT = 6,          /* a bounded device wait (~1 s; the mixed force kernel's wait
+                                    for a list copy) ran out; the step was abandoned, the
+                                    state is undefined: destroy the context */
     MD_ERR_CUDA = 7,             /* a CUDA runtime call failed (message has the CUDA error) */
     MD_ERR_NOMEM = 8             /* device or host allocation failed */
 } md_status;
@@ -206,6 +208,12 @@ md_status md_profile_read(md_ctx *ctx, int64_t *launches, double *ms, double *al
 /* Number of library kernels enqueued on this context since creation (graph
  * replays count every kernel node of the replayed graph). */
 md_status md_launch_count(md_ctx *ctx, int64_t *kernels);
+
+/* Test hook for the timeout path, off by default: with on != 0 the mixed force
+ * kernel arms each list-copy barrier for 16 bytes more than it copies, so its
+ * bounded waits run out and the call returns MD_ERR_TIMEOUT (no device fault,
+ * no unbounded wait).  Not for production use. */
+md_status md_debug_expire_waits(md_ctx *ctx, int32_t on);
 
 const char *md_last_error(const md_ctx *ctx);
 void md_destroy(md_ctx *ctx);

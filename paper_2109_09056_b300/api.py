@@ -261,6 +261,11 @@ def md_launch_count(ctx: Ctx) -> int:
     return k.value
 
 
+def md_debug_expire_waits(ctx: Ctx, on: bool = True) -> None:
+    """Test hook: make the mixed force kernel's bounded list-copy waits run out."""
+    check(lib.md_debug_expire_waits(ctx.handle, 1 if on else 0), ctx.handle)
+
+
 def md_bin_sort_noalloc(box, x, rs: float, perm, stream=None) -> None:
     """Binning + stable cell-order permutation into the caller's device array
     `perm` without any device allocation (x and perm must be CUDA tensors)."""

@@ -137,7 +137,6 @@ md_status setup_pair(md_ctx *c, const double *eps, const double *sigma) {
                 const double c2 = (s * s) / P.rc2, c6 = c2 * c2 * c2;
                 P.ush[ab] = 4.0 * e * (c6 * c6 - c6);
             }
-            P.fe24[ab] = (float)P.e24[ab];
             P.fs2[ab] = (float)P.s2[ab];
             P.fe4[ab] = (float)P.e4[ab];
             P.fush[ab] = (float)P.ush[ab];
@@ -945,6 +944,13 @@ md_status md_profile_read(md_ctx *c, int64_t *launches, double *ms, double *alg_
 md_status md_launch_count(md_ctx *c, int64_t *kernels) {
     if (!c || !kernels) return MD_ERR_ARG;
     *kernels = c->kernels;
+    return MD_OK;
+}
+
+md_status md_debug_expire_waits(md_ctx *c, int32_t on) {
+    if (!c) return MD_ERR_ARG;
+    c->debug_tx_extra = on ? 16u : 0u;
+    invalidate_graphs(c);  // captured launches carry the old value
     return MD_OK;
 }
 

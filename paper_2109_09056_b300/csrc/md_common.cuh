@@ -39,30 +39,14 @@
 #ifndef MD_FORCE_MINB
 #define MD_FORCE_MINB 6   // measured best on B300 at 4M atoms (5: 1.03 ms, 6: 0.94 ms)
 #endif
-// List rows: 1 = loaded into registers one batch ahead; 0 = a whole tile's rows
-// staged in a shared-memory double buffer with cp.async; 2 = the same buffer
-// filled by one bulk (TMA) copy per tile.
+// List rows of a warp-tile into its shared-memory buffer: 1 = one bulk (TMA)
+// copy completing on an mbarrier; 0 = the warp's 16-byte cp.async copies.
 #ifndef MD_FORCE_LIST
 #define MD_FORCE_LIST 1
 #endif
-// Terms combined by an FMA chain before each Kahan add (1, 2 or 4).
-#ifndef MD_FORCE_KSUM
-#define MD_FORCE_KSUM 1
-#endif
-// 1: rows past the last whole batch are evaluated one at a time instead of
-// rounding a tile's row count up to a whole batch.
-#ifndef MD_FORCE_TAIL
-#define MD_FORCE_TAIL 1
-#endif
-// Stencil offset of a list entry: 0 = a 27-entry float4 table in shared
-// memory; 1 = three warp shuffles from the lanes holding the table.
-#ifndef MD_FORCE_OFFSET
-#define MD_FORCE_OFFSET 0
-#endif
-// Merge of an atom's T lane sums: 0 = TwoSum on (sum, compensation) pairs;
-// 1 = each lane folds its compensation, then a plain xor-shuffle sum.
-#ifndef MD_FORCE_MERGE
-#define MD_FORCE_MERGE 0
+// List terms combined by an FMA chain before each Kahan add (divides MD_FORCE_BATCH).
+#ifndef MD_FORCE_GROUP
+#define MD_FORCE_GROUP 4
 #endif
 
 namespace mdb {
@@ -100,8 +84,8 @@ struct Pair {
     float rc2f, rs2f, bandf, pad_;
     double eps[64], sig[64];
     double e24[64], s2[64], e4[64], ush[64];  // 24 eps, sigma^2, 4 eps, U(rc) (0 if unshifted)
-    float fe24[64], fs2[64], fe4[64], fush[64];
-    float fc1[64];  // 24 eps / sigma^2
+    float fs2[64], fe4[64], fush[64];  // sigma^2, 4 eps, U(rc) in FP32
+    float fc1[64];                      // 24 eps / sigma^2 in FP32
     double mass[MD_MAXT], dtm[MD_MAXT], hdtm[MD_MAXT];
 };
 
@@ -210,6 +194,7 @@ struct md_ctx {
     size_t ev_used = 0;
     int64_t prof_launches = 0;
     int64_t kernels = 0;           // library kernels enqueued (see md_launch_count)
+    uint32_t debug_tx_extra = 0;   // md_debug_expire_waits
     double prof_ms = 0.0;
     double prof_bytes = 0.0;
 

@@ -52,6 +52,7 @@ struct ForceArgs {
     int mode;
     int thermo_every;
     unsigned int *done;
+    uint32_t tx_extra;  // test hook: list-copy bytes that never arrive (0 normally)
 };
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float t) {
@@ -59,21 +60,6 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float t) {
     const float u = s + y;
     c = (u - s) - y;
     s = u;
-}
-
-// Merge (s, c) pairs (value = s - c) of the T lanes of an atom with TwoSum.
-template <int T>
-__device__ __forceinline__ void merge_lanes(float &s, float &c) {
-#pragma unroll
-    for (int o = T / 2; o >= 1; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-        const float S = s + s2;
-        const float bp = S - s;
-        const float err = (s - (S - bp)) + (s2 - bp);
-        c = (c + c2) - err;
-        s = S;
-    }
 }
 
 template <int T>
@@ -96,7 +82,7 @@ __device__ __forceinline__ double warp_max_d(double x) {
 
 // Shared per-CTA tables.
 struct SmemTabs {
-    float fe24[64], fs2[64], fe4[64], fush[64], fc1[64];
+    float fs2[64], fe4[64], fush[64], fc1[64];
     double de24[64], ds2[64], de4[64], dush[64];
     double dtm[MD_MAXT], hdtm[MD_MAXT], mass[MD_MAXT];
 };
@@ -151,18 +137,65 @@ __device__ __forceinline__ float epilogue(const ForceArgs &a, const SmemTabs &tb
     return snew;
 }
 
-template <bool MIXED, int T, bool ONE, bool THERMO>
-__device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &tb,
-                                           float4 (*s_offf)[27], double (*s_offd)[81]) {
+
+// The rest of a warp-tile once each atom's force is known in all its lanes:
+// the velocity-Verlet epilogue (lane `sub` takes components sub, sub + T, ...),
+// the atom's next shadow, and the tile's thermo partials.
+template <int T, bool THERMO, typename FT>
+__device__ __forceinline__ void finish_tile(const ForceArgs &a, const SmemTabs &tb, int64_t wt,
+                                            int64_t i, bool valid, int ti, const FT (&F)[3],
+                                            double ped) {
+    const int lane = threadIdx.x & 31, sub = lane % T;
+    double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
+    float snew[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < (3 + T - 1) / T; ++k) {
+        const int d = sub + k * T;
+        if (valid && d < 3) {
+            const double Fc = (double)(d == 0 ? F[0] : (d == 1 ? F[1] : F[2]));
+            double pp = 0.0;
+            const float sn = epilogue<THERMO>(a, tb, i, d, ti, Fc, ke, pp, disp2);
+#pragma unroll
+            for (int dd = 0; dd < 3; ++dd)
+                if (dd == d) { snew[dd] = sn; pd[dd] = pp; }
+        }
+    }
+    if (a.mode == MODE_FUSED) {
+        float s3[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            s3[d] = __shfl_sync(0xffffffffu, snew[d], (lane - sub) + d % T);
+        if (valid && sub == 0) a.sh_out[i] = make_float4(s3[0], s3[1], s3[2], __int_as_float(ti));
+    }
+    if (THERMO) {
+        // displacement^2 of the atom = sum over its components (spread over lanes)
+        const double dsum = sum_lanes_d<T>(disp2);
+        const double pe_t = warp_sum_d((valid && sub == 0) ? ped : 0.0);
+        const double ke_t = warp_sum_d(ke);
+        const double px = warp_sum_d(pd[0]), py = warp_sum_d(pd[1]), pz = warp_sum_d(pd[2]);
+        const double dm = warp_max_d(valid ? dsum : 0.0);
+        if (lane == 0) {
+            double *tp = a.tpart + wt * TP;
+            tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
+        }
+    }
+}
+
+// ---- FP64 kernel ----
+//
+// Warp w of the grid takes warp-tiles w, w + nwarps, ...; each lane walks its
+// share of the atom's row (entries sub, sub + T, ...) kBatch entries at a time:
+// the list words, then the neighbor positions, then the pair terms.
+template <int T, bool ONE, bool THERMO>
+__device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs &tb,
+                                             double (*s_offd)[81]) {
     constexpr int A = 32 / T;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int sub = lane % T;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int nt = a.pair->nt;
-    const float rc2f = a.pair->rc2f;
     const double rc2 = a.pair->rc2;
-    const float e24_0 = tb.fe24[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
     const double de24_0 = tb.de24[0], ds2_0 = tb.ds2[0], de4_0 = tb.de4[0], dush_0 = tb.dush[0];
     int curbox = -1;
     for (int64_t wt = gw; wt < a.nwt; wt += nw) {
@@ -172,14 +205,9 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
         if (b != curbox) {
             if (lane < 27) {
                 const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-                if (MIXED) {
-                    s_offf[wib][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
-                                                    (float)oz * B.hf[2], 0.f);
-                } else {
-                    s_offd[wib][3 * lane + 0] = (double)ox * B.h[0];
-                    s_offd[wib][3 * lane + 1] = (double)oy * B.h[1];
-                    s_offd[wib][3 * lane + 2] = (double)oz * B.h[2];
-                }
+                s_offd[wib][3 * lane + 0] = (double)ox * B.h[0];
+                s_offd[wib][3 * lane + 1] = (double)oy * B.h[1];
+                s_offd[wib][3 * lane + 2] = (double)oz * B.h[2];
             }
             __syncwarp();
             curbox = b;
@@ -187,71 +215,26 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
         const bool valid = (i - B.slot_off) < B.n;
         const int ni = valid ? min(a.nn[i], a.pad) : 0;
         const uint32_t *row = a.nbr + (size_t)wt * a.R * 32 + lane;
-        double Fd[3];
-        double ped = 0.0;
-        int ti;
-        if (MIXED) {
-            const float4 si = a.sh_in[i];
-            ti = ONE ? 0 : __float_as_int(si.w);
-            float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
-            int q = 0;
-            for (int k = sub; k < ni; k += T, ++q) {
-                const uint32_t e = __ldcs(row + (size_t)q * 32);
-                const uint32_t j = e & MD_IDX_MASK;
-                const float4 sj = __ldg(a.sh_in + j);
-                const float4 o = s_offf[wib][e >> MD_IDX_BITS];
-                const float dx = (sj.x + o.x) - si.x;
-                const float dy = (sj.y + o.y) - si.y;
-                const float dz = (sj.z + o.z) - si.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < rc2f) {
-                    float e24, s2, e4, ush;
-                    if (ONE) {
-                        e24 = e24_0; s2 = s2_0; e4 = e4_0; ush = ush_0;
-                    } else {
-                        const int ab = ti * nt + __float_as_int(sj.w);
-                        e24 = tb.fe24[ab]; s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
-                    }
-                    const float r2inv = __fdividef(1.0f, r2);
-                    const float q2 = s2 * r2inv;
-                    const float s6 = q2 * q2 * q2;
-                    const float phi = e24 * r2inv * s6 * fmaf(2.0f, s6, -1.0f);
-                    kahan_add(fx, cx, -phi * dx);
-                    kahan_add(fy, cy, -phi * dy);
-                    kahan_add(fz, cz, -phi * dz);
-                    if (THERMO) kahan_add(pe, cp, 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush));
-                }
+        const double rix = a.r_in[i], riy = a.r_in[a.ns + i], riz = a.r_in[2 * a.ns + i];
+        const int ti = ONE ? 0 : a.type[i];
+        double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
+        const int nq = (ni - sub + T - 1) / T;
+        for (int q0 = 0; q0 < nq; q0 += kBatch) {
+            uint32_t e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                e[u] = (q0 + u < nq) ? __ldcs(row + (size_t)(q0 + u) * 32) : kNoEntry;
+            double xj[kBatch], yj[kBatch], zj[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const uint32_t j = e[u] & MD_IDX_MASK;
+                const bool ok = e[u] != kNoEntry;
+                xj[u] = ok ? __ldg(a.r_in + j) : 1e4;
+                yj[u] = ok ? __ldg(a.r_in + a.ns + j) : 1e4;
+                zj[u] = ok ? __ldg(a.r_in + 2 * a.ns + j) : 1e4;
             }
-            merge_lanes<T>(fx, cx);
-            merge_lanes<T>(fy, cy);
-            merge_lanes<T>(fz, cz);
-            Fd[0] = (double)fx; Fd[1] = (double)fy; Fd[2] = (double)fz;
-            if (THERMO) {
-                merge_lanes<T>(pe, cp);
-                ped = (double)pe;
-            }
-        } else {
-            const double rix = a.r_in[i], riy = a.r_in[a.ns + i], riz = a.r_in[2 * a.ns + i];
-            ti = ONE ? 0 : a.type[i];
-            double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
-            // batches of kBatch entries per lane: list words, then positions, then math
-            const int nq = (ni - sub + T - 1) / T;
-            for (int q0 = 0; q0 < nq; q0 += kBatch) {
-              uint32_t e[kBatch];
 #pragma unroll
-              for (int u = 0; u < kBatch; ++u)
-                  e[u] = (q0 + u < nq) ? __ldcs(row + (size_t)(q0 + u) * 32) : kNoEntry;
-              double xj[kBatch], yj[kBatch], zj[kBatch];
-#pragma unroll
-              for (int u = 0; u < kBatch; ++u) {
-                  const uint32_t j = e[u] & MD_IDX_MASK;
-                  const bool ok = e[u] != kNoEntry;
-                  xj[u] = ok ? __ldg(a.r_in + j) : 1e4;
-                  yj[u] = ok ? __ldg(a.r_in + a.ns + j) : 1e4;
-                  zj[u] = ok ? __ldg(a.r_in + 2 * a.ns + j) : 1e4;
-              }
-#pragma unroll
-              for (int u = 0; u < kBatch; ++u) {
+            for (int u = 0; u < kBatch; ++u) {
                 const uint32_t j = e[u] & MD_IDX_MASK;
                 const double *o = s_offd[wib] + 3 * ((e[u] >> MD_IDX_BITS) % 27);
                 const double dx = (xj[u] + o[0]) - rix;
@@ -275,99 +258,49 @@ __device__ __forceinline__ void force_body(const ForceArgs &a, const SmemTabs &t
                     fz -= phi * dz;
                     if (THERMO) pe += 0.5 * (e4 * s6 * (s6 - 1.0) - ush);
                 }
-              }
-            }
-            Fd[0] = sum_lanes_d<T>(fx);
-            Fd[1] = sum_lanes_d<T>(fy);
-            Fd[2] = sum_lanes_d<T>(fz);
-            if (THERMO) ped = sum_lanes_d<T>(pe);
-        }
-        // Epilogue: lane `sub` handles components sub, sub + T, ...
-        double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
-        float snew[3] = {0.f, 0.f, 0.f};
-        if (valid) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (d % T == sub) {
-                    double pp = 0.0;
-                    snew[d] = epilogue<THERMO>(a, tb, i, d, ti, Fd[d], ke, pp, disp2);
-                    pd[d] = pp;
-                }
             }
         }
-        if (a.mode == MODE_FUSED) {
-            float s3[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                s3[d] = __shfl_sync(0xffffffffu, snew[d], (lane - sub) + d % T);
-            if (valid && sub == 0) a.sh_out[i] = make_float4(s3[0], s3[1], s3[2], __int_as_float(ti));
-        }
-        if (THERMO) {
-            // displacement^2 of the atom = sum over its components (spread over lanes)
-            const double dsum = sum_lanes_d<T>(disp2);
-            const double pe_t = warp_sum_d((valid && sub == 0) ? ped : 0.0);
-            const double ke_t = warp_sum_d(ke);
-            const double px = warp_sum_d(pd[0]), py = warp_sum_d(pd[1]), pz = warp_sum_d(pd[2]);
-            const double dm = warp_max_d(valid ? dsum : 0.0);
-            if (lane == 0) {
-                double *tp = a.tpart + wt * TP;
-                tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
-            }
-        }
+        const double Fd[3] = {sum_lanes_d<T>(fx), sum_lanes_d<T>(fy), sum_lanes_d<T>(fz)};
+        const double ped = THERMO ? sum_lanes_d<T>(pe) : 0.0;
+        finish_tile<T, THERMO>(a, tb, wt, i, valid, ti, Fd, ped);
     }
 }
 
 // ---- mixed-precision kernel ----
 //
 // Each warp walks a contiguous run of warp-tiles (the CTA's chunk, warps
-// interleaved, so the CTA's warps share neighbors in L1).  List rows are read
-// one batch ahead of their use, so only the neighbor gathers wait on memory:
-// with MD_FORCE_LIST 1 straight into registers (the batch after the current
-// one; at a tile's end, the next tile's first batch), with MD_FORCE_LIST 0 a
-// whole tile's rows at a time into a per-warp shared-memory double buffer
-// (cp.async).  Neighbor shadows are gathered kBatch at a time per lane.
+// interleaved, so the CTA's warps share neighbors in L1).  While it evaluates
+// tile t it has tile t + 1's list rows in flight into the other half of a
+// per-warp shared-memory double buffer: one bulk (TMA) copy per tile that
+// completes on an mbarrier (MD_FORCE_LIST 1), or 16-byte cp.async copies
+// (MD_FORCE_LIST 0); only as many 128-byte rows as the tile's longest row.
+// Neighbor shadows are gathered kBatch at a time per lane.
 
-// The list is read once per step: its loads carry an L2 evict-first policy so
+// The list is read once per step: its copies carry an L2 evict-first policy so
 // they do not push out the neighbor shadows (small enough to stay in L2).
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
     return pol;
 }
-__device__ __forceinline__ uint32_t ld_list(const uint32_t *p, uint64_t pol) {
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;\n"
-        : "=r"(v)
-        : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint64_t pol) {
-    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(saddr),
-                 "l"(g), "l"(pol)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
-// MD_FORCE_LIST 2: a tile's rows as one bulk (TMA) copy completing on an mbarrier.
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
-// rows [0, rows) of a list block (128 bytes each) -> shared dst; lane 0 only
+// Rows [0, rows) of a list block (128 bytes each) -> shared dst as one bulk
+// copy that completes on mbarrier `bar` (the arrival and the byte count are
+// posted together).  `extra` adds bytes that never arrive: a test hook that
+// makes the wait below run out.  One lane only.
 __device__ __forceinline__ void bulk_rows(uint32_t dst, const uint32_t *src, int rows, uint32_t bar,
-                                          uint64_t pol) {
+                                          uint64_t pol, uint32_t extra) {
     const uint32_t bytes = (uint32_t)rows * 128u;
-    // the warp's earlier generic reads of dst come before the async-proxy write
+    // the warp's earlier generic-proxy reads of dst come before the async-proxy write
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                 "r"(bytes + extra)
                  : "memory");
     if (bytes > 0)
         asm volatile(
@@ -391,7 +324,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
     return t;
 }
-// Wait for the phase with the given parity to complete; false after ~1 s.
+// Wait for the mbarrier phase of the given parity; false after ~1 s (or 2^28
+// polls), so a copy that never completes cannot hang the kernel.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
@@ -402,22 +336,29 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// Rows [0, rows) of warp-tile wt's list block -> dst (rows * 32 words).
-__device__ __forceinline__ void prefetch_rows(const uint32_t *nbr, int64_t wt, int R, int rows,
-                                              uint32_t *dst, int lane) {
-    const uint32_t *src = nbr + (size_t)wt * R * 32;
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
-    const uint64_t pol = l2_evict_first_policy();
-    for (int c = lane; c < rows * 8; c += 32) cp_async16(s + 16u * c, src + 4 * c, pol);
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint64_t pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(saddr),
+                 "l"(g), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// Rows [0, rows) of a list block -> shared dst with the whole warp's cp.async.
+__device__ __forceinline__ void cp_async_rows(uint32_t dst, const uint32_t *src, int rows, int lane,
+                                              uint64_t pol) {
+    for (int c = lane; c < rows * 8; c += 32) cp_async16(dst + 16u * c, src + 4 * c, pol);
 }
 
 // List rows a warp-tile needs: its longest row (rows past an atom's count hold
-// the sentinel entry), rounded up to whole batches unless the rows past the
-// last whole batch are evaluated one at a time.
+// the sentinel entry).
 template <int T>
 __device__ __forceinline__ int tile_rows(int ni) {
-    const int r = __reduce_max_sync(0xffffffffu, (ni + T - 1) / T);
-    return MD_FORCE_TAIL ? r : (r + kBatch - 1) / kBatch * kBatch;
+    return __reduce_max_sync(0xffffffffu, (ni + T - 1) / T);
 }
 
 template <int T>
@@ -432,8 +373,8 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
                                            float4 (*s_off)[32], uint64_t (*s_bar)[2],
                                            uint32_t *lbuf) {
     constexpr int A = 32 / T;
-    constexpr int G = MD_FORCE_KSUM;
-    static_assert(kBatch % G == 0, "MD_FORCE_KSUM must divide MD_FORCE_BATCH");
+    constexpr int G = MD_FORCE_GROUP;
+    static_assert(kBatch % G == 0, "MD_FORCE_GROUP must divide MD_FORCE_BATCH");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, sub = lane % T;
     const int nwc = blockDim.x >> 5;
     const int64_t chunk = (a.nwt + gridDim.x - 1) / gridDim.x;
@@ -444,24 +385,10 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     const float c1_0 = tb.fc1[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
     const float c1x2_0 = 2.0f * c1_0;
     const size_t rowblk = (size_t)a.R * 32;  // words in one warp-tile's list block
-    int64_t wt = t0 + wib;
-#if MD_FORCE_LIST == 1
-    (void)lbuf;
     const uint64_t pol = l2_evict_first_policy();
-    uint32_t e[kBatch];  // the next batch of this lane's entries, already loaded
-    int nn_cur = 0;
-    if (wt < t1) {
-        nn_cur = __ldg(a.nn + wt * A + lane / T);
-        const uint32_t *L0 = a.nbr + wt * rowblk + lane;
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) e[u] = ld_list(L0 + u * 32, pol);
-    }
-#else
-    uint32_t *const buf0 = lbuf + (size_t)wib * 2 * rowblk;
-    int rows_cur = 0;
-#if MD_FORCE_LIST == 2
-    const uint64_t pol = l2_evict_first_policy();
-    const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(buf0);
+    const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(lbuf + (size_t)wib * 2 * rowblk);
+    const uint32_t bstride = (uint32_t)(rowblk * 4);  // bytes per buffer half
+#if MD_FORCE_LIST
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[wib][0]);
     uint32_t phase = 0;  // bit k: parity of buffer k's next completion
     if (lane == 0) {
@@ -470,71 +397,61 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         fence_mbar_init();
     }
     __syncwarp();
-    if (wt < t1) {
-        rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
-        if (lane == 0) bulk_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, bar0, pol);
-    }
 #else
+    (void)s_bar;
+#endif
+    int64_t wt = t0 + wib;
+    int rows_cur = 0;
     if (wt < t1) {
         rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
-        prefetch_rows(a.nbr, wt, a.R, rows_cur, buf0, lane);
+#if MD_FORCE_LIST
+        if (lane == 0) bulk_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, bar0, pol, a.tx_extra);
+#else
+        cp_async_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, lane, pol);
+#endif
     }
+#if !MD_FORCE_LIST
     cp_async_commit();
 #endif
     int cb = 0;
-#endif
     int curbox = -1;
-    float ofx = 0.f, ofy = 0.f, ofz = 0.f;  // MD_FORCE_OFFSET 1: lane k holds code k's offset
     for (; wt < t1; wt += nwc) {
         const int64_t wn = wt + nwc;
         const bool has_next = wn < t1;
-#if MD_FORCE_LIST == 1
-        const int nn_next = has_next ? __ldg(a.nn + wn * A + lane / T) : 0;
-        const int rows_cur = tile_rows<T>(min(nn_cur, a.pad));
-        const uint32_t *Lc = a.nbr + wt * rowblk + lane;
-        const uint32_t *Ln = a.nbr + wn * rowblk + lane;  // read only if has_next
-#else
         int rows_next = 0;
         if (has_next) {
             rows_next = tile_rows<T>(min(__ldg(a.nn + wn * A + lane / T), a.pad));
-#if MD_FORCE_LIST == 2
+#if MD_FORCE_LIST
             if (lane == 0)
-                bulk_rows(sbuf0 + (uint32_t)((cb ^ 1) * rowblk * 4), a.nbr + wn * rowblk, rows_next,
-                          bar0 + 8 * (cb ^ 1), pol);
+                bulk_rows(sbuf0 + (cb ^ 1) * bstride, a.nbr + wn * rowblk, rows_next,
+                          bar0 + 8 * (cb ^ 1), pol, a.tx_extra);
 #else
-            prefetch_rows(a.nbr, wn, a.R, rows_next, buf0 + (cb ^ 1) * rowblk, lane);
+            cp_async_rows(sbuf0 + (cb ^ 1) * bstride, a.nbr + wn * rowblk, rows_next, lane, pol);
 #endif
         }
-#if MD_FORCE_LIST == 0
+#if !MD_FORCE_LIST
         cp_async_commit();
-#endif
 #endif
         const int64_t i = wt * A + lane / T;
         const int b = a.tile_box[(wt * A) >> 5];
         const Box &B = a.boxes[b];
         if (b != curbox) {
-            // stencil offset of code `lane` (codes 27..31 unused: zero)
-            float4 ol = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (lane < 27) {
+            if (lane >= 27) {
+                s_off[wib][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
                 const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-                ol = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1], (float)oz * B.hf[2], 0.f);
+                s_off[wib][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
+                                               (float)oz * B.hf[2], 0.f);
             }
-#if MD_FORCE_OFFSET
-            ofx = ol.x; ofy = ol.y; ofz = ol.z;
-#else
-            s_off[wib][lane] = ol;
-#endif
             curbox = b;
         }
         const bool valid = (i - B.slot_off) < B.n;
         const float4 si = a.sh_in[i];
         const int ti = ONE ? 0 : __float_as_int(si.w);
-#if MD_FORCE_LIST == 1
-        __syncwarp();  // s_off is visible to the whole warp
-#else
-#if MD_FORCE_LIST == 2
-        // the current tile's rows have landed (bounded wait: on expiry the
-        // step is abandoned with a timeout status)
+#if MD_FORCE_LIST
+        // the current tile's rows have landed; a wait that runs out abandons
+        // the step with a timeout status (after waiting, again bounded, for
+        // the copy in flight into the other half)
         if (!mbar_wait(bar0 + 8 * cb, (phase >> cb) & 1u)) {
             atomicOr(&a.fl->status, ST_TIMEOUT);
             if (has_next) mbar_wait(bar0 + 8 * (cb ^ 1), (phase >> (cb ^ 1)) & 1u);
@@ -544,31 +461,22 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
 #else
         cp_async_wait<1>();  // this lane's copies of the current tile have landed
 #endif
-        __syncwarp();        // ... and every other lane's; s_off is visible too
-        const uint32_t *Lr = buf0 + cb * rowblk + lane;
-#endif
+        __syncwarp();  // ... and every other lane's; s_off is visible too
+        const uint32_t *Lr = lbuf + (size_t)wib * 2 * rowblk + cb * rowblk + lane;
         float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
         // One list entry: x_j - x_i from the shadows and the stencil offset,
         // the LJ term masked at rc (sentinel entries past an atom's count sit
         // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
         auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
                          float &tp) {
-#if MD_FORCE_OFFSET
-            const int code = (int)(en >> MD_IDX_BITS);
-            float4 o;
-            o.x = __shfl_sync(0xffffffffu, ofx, code);
-            o.y = __shfl_sync(0xffffffffu, ofy, code);
-            o.z = __shfl_sync(0xffffffffu, ofz, code);
-#else
             const float4 o = s_off[wib][en >> MD_IDX_BITS];
-#endif
             const float dx = (sj.x + o.x) - si.x;
             const float dy = (sj.y + o.y) - si.y;
             const float dz = (sj.z + o.z) - si.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const bool in = r2 < rc2f;
-            float s2, e4, ush, w;
             const float r2inv = __fdividef(1.0f, r2);
+            float s2, e4, ush, w;
             if (ONE) {
                 s2 = s2_0; e4 = e4_0; ush = ush_0;
             } else {
@@ -577,12 +485,10 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             }
             const float q2 = s2 * r2inv;
             const float s6 = q2 * q2 * q2;
-            // phi = 24 eps / r^2 (sigma/r)^6 [2 (sigma/r)^6 - 1] = c1 q2 s6 (2 s6 - 1)
-            if (ONE) {
-                w = fmaf(c1x2_0, s6, -c1_0);
-            } else {
-                w = tb.fc1[ti * nt + __float_as_int(sj.w)] * fmaf(2.0f, s6, -1.0f);
-            }
+            // phi = 24 eps / r^2 (sigma/r)^6 [2 (sigma/r)^6 - 1] = c1 q2 s6 (2 s6 - 1),
+            // c1 = 24 eps / sigma^2
+            if (ONE) w = fmaf(c1x2_0, s6, -c1_0);
+            else w = tb.fc1[ti * nt + __float_as_int(sj.w)] * fmaf(2.0f, s6, -1.0f);
             const float phi = in ? (q2 * s6) * w : 0.0f;
             tx = -phi * dx;
             ty = -phi * dy;
@@ -590,7 +496,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             tp = (THERMO && in) ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f;
         };
         // groups of G consecutive terms are added by an FMA chain, each group
-        // sum by one Kahan step
+        // sum into the lane's partial by one Kahan step
         auto batch = [&](const uint32_t (&eb)[kBatch], const float4 (&sj)[kBatch]) {
             float gx = 0.f, gy = 0.f, gz = 0.f, gp = 0.f;
 #pragma unroll
@@ -610,41 +516,8 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
                 }
             }
         };
-        auto single = [&](const uint32_t en) {
-            const float4 sj = __ldg(a.sh_in + (en & MD_IDX_MASK));
-            float tx, ty, tz, tp;
-            terms(en, sj, tx, ty, tz, tp);
-            kahan_add(fx, cx, tx);
-            kahan_add(fy, cy, ty);
-            kahan_add(fz, cz, tz);
-            if (THERMO) kahan_add(pe, cp, tp);
-        };
-        const int rows_full = rows_cur / kBatch * kBatch;  // == rows_cur unless MD_FORCE_TAIL
-#if MD_FORCE_LIST == 1
-        for (int q = 0; q < rows_full; q += kBatch) {
-            float4 sj[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (e[u] & MD_IDX_MASK));
-            // the batch after this one: this tile's next rows, else the next tile's first
-            const bool more = q + kBatch < rows_full;
-            uint32_t en[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) en[u] = e[u];
-            if (more || has_next) {
-                const uint32_t *P = more ? Lc + (size_t)(q + kBatch) * 32 : Ln;
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) en[u] = ld_list(P + u * 32, pol);
-            }
-            batch(e, sj);
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) e[u] = en[u];
-        }
-        if (rows_full == 0 && has_next) {
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) e[u] = ld_list(Ln + u * 32, pol);
-        }
-        for (int q = rows_full; q < rows_cur; ++q) single(ld_list(Lc + (size_t)q * 32, pol));
-#else
+        // whole batches, then the remaining rows one at a time
+        const int rows_full = rows_cur / kBatch * kBatch;
         for (int q = 0; q < rows_full; q += kBatch) {
             uint32_t eb[kBatch];
 #pragma unroll
@@ -654,72 +527,64 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (eb[u] & MD_IDX_MASK));
             batch(eb, sj);
         }
-        for (int q = rows_full; q < rows_cur; ++q) single(Lr[q * 32]);
-        __syncwarp();  // done reading buf[cb]; the next prefetch may refill it
-#endif
-#if MD_FORCE_MERGE
-        fx = sum_lanes_f<T>(fx - cx);
-        fy = sum_lanes_f<T>(fy - cy);
-        fz = sum_lanes_f<T>(fz - cz);
-        double ped = 0.0;
-        if (THERMO) ped = (double)sum_lanes_f<T>(pe - cp);
-#else
-        merge_lanes<T>(fx, cx);
-        merge_lanes<T>(fy, cy);
-        merge_lanes<T>(fz, cz);
-        fx -= cx;
-        fy -= cy;
-        fz -= cz;
-        double ped = 0.0;
-        if (THERMO) {
-            merge_lanes<T>(pe, cp);
-            ped = (double)(pe - cp);
+        for (int q = rows_full; q < rows_cur; ++q) {
+            const uint32_t en = Lr[q * 32];
+            const float4 sj = __ldg(a.sh_in + (en & MD_IDX_MASK));
+            float tx, ty, tz, tp;
+            terms(en, sj, tx, ty, tz, tp);
+            kahan_add(fx, cx, tx);
+            kahan_add(fy, cy, ty);
+            kahan_add(fz, cz, tz);
+            if (THERMO) kahan_add(pe, cp, tp);
         }
-#endif
-        // Epilogue: one FP64 update per component, the components spread over
-        // the atom's lanes (lane sub takes components sub, sub + T, ...).
-        double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
-        float snew[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < (3 + T - 1) / T; ++k) {
-            const int d = sub + k * T;
-            if (valid && d < 3) {
-                const float Fs = d == 0 ? fx : (d == 1 ? fy : fz);
-                double pp = 0.0;
-                const float sn = epilogue<THERMO>(a, tb, i, d, ti, (double)Fs, ke, pp, disp2);
-#pragma unroll
-                for (int dd = 0; dd < 3; ++dd)
-                    if (dd == d) { snew[dd] = sn; pd[dd] = pp; }
-            }
-        }
-        if (a.mode == MODE_FUSED) {
-            float s3[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                s3[d] = __shfl_sync(0xffffffffu, snew[d], (lane - sub) + d % T);
-            if (valid && sub == 0) a.sh_out[i] = make_float4(s3[0], s3[1], s3[2], __int_as_float(ti));
-        }
-        if (THERMO) {
-            const double dsum = sum_lanes_d<T>(disp2);
-            const double pe_t = warp_sum_d((valid && sub == 0) ? ped : 0.0);
-            const double ke_t = warp_sum_d(ke);
-            const double px = warp_sum_d(pd[0]), py = warp_sum_d(pd[1]), pz = warp_sum_d(pd[2]);
-            const double dm = warp_max_d(valid ? dsum : 0.0);
-            if (lane == 0) {
-                double *tp = a.tpart + wt * TP;
-                tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
-            }
-        }
-#if MD_FORCE_LIST == 1
-        nn_cur = nn_next;
-#else
+        __syncwarp();  // done reading this half; the next copy may refill it
+        // each lane folds its compensation (value = s - c); the T lane
+        // partials of an atom are then added in a fixed xor-shuffle order
+        const double Fd[3] = {(double)sum_lanes_f<T>(fx - cx), (double)sum_lanes_f<T>(fy - cy),
+                              (double)sum_lanes_f<T>(fz - cz)};
+        const double ped = THERMO ? (double)sum_lanes_f<T>(pe - cp) : 0.0;
+        finish_tile<T, THERMO>(a, tb, wt, i, valid, ti, Fd, ped);
         cb ^= 1;
         rows_cur = rows_next;
-#endif
     }
-#if MD_FORCE_LIST == 0
+#if !MD_FORCE_LIST
     cp_async_wait<0>();
 #endif
+}
+
+// Frozen (a list overflowed, a position went non-finite or a wait ran out
+// earlier in this run): keep the state and mirror it into the output buffers
+// so the buffer flip stays valid.
+__device__ __forceinline__ void mirror_state(const ForceArgs &a) {
+    if (a.mode != MODE_FUSED) return;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        a.sh_out[t] = a.sh_in[t];
+        for (int d = 0; d < 3; ++d) a.r_out[d * a.ns + t] = a.r_in[d * a.ns + t];
+    }
+}
+
+__device__ __forceinline__ void load_tabs(const Pair &P, SmemTabs &tb) {
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+        tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t]; tb.fc1[t] = P.fc1[t];
+        tb.de24[t] = P.e24[t]; tb.ds2[t] = P.s2[t]; tb.de4[t] = P.e4[t]; tb.dush[t] = P.ush[t];
+        if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
+    }
+}
+
+// The last CTA to finish records which step the thermo partials describe and,
+// in FUSED mode, advances the step clock (every CTA has read it).
+__device__ __forceinline__ void kernel_done(const ForceArgs &a, int64_t clock, bool thermo) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(a.done, 1u);
+        if (prev == gridDim.x - 1) {
+            *a.done = 0u;
+            a.fl->thermo = thermo ? 1u : 0u;
+            if (a.mode == MODE_FUSED) a.fl->clock = clock + 1;
+        }
+    }
 }
 
 template <int T, bool ONE>
@@ -727,83 +592,37 @@ template <int T, bool ONE>
 // per-thread budget serves 64- and 256-thread CTAs).
 __global__ void __launch_bounds__(256, (MD_FORCE_MINB + 1) / 2) k_force_mixed(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
-        if (a.mode == MODE_FUSED) {
-            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
-                 t += (int64_t)gridDim.x * blockDim.x) {
-                a.sh_out[t] = a.sh_in[t];
-                for (int d = 0; d < 3; ++d) a.r_out[d * a.ns + t] = a.r_in[d * a.ns + t];
-            }
-        }
+        mirror_state(a);
         return;
     }
     extern __shared__ __align__(128) uint32_t lbuf[];
     __shared__ SmemTabs tb;
     __shared__ __align__(16) float4 s_off[8][32];
     __shared__ __align__(8) uint64_t s_bar[8][2];
-    const Pair &P = *a.pair;
-    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
-        tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
-        tb.fc1[t] = P.fc1[t];
-        if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
-    }
+    load_tabs(*a.pair, tb);
     __syncthreads();
     const int64_t clock = a.fl->clock;
     const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
     if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, s_bar, lbuf);
     else mixed_body<T, ONE, false>(a, tb, s_off, s_bar, lbuf);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int prev = atomicAdd(a.done, 1u);
-        if (prev == gridDim.x - 1) {
-            *a.done = 0u;
-            a.fl->thermo = thermo ? 1u : 0u;
-            if (a.mode == MODE_FUSED) a.fl->clock = clock + 1;
-        }
-    }
+    kernel_done(a, clock, thermo);
 }
 
-template <bool MIXED, int T, bool ONE>
-__global__ void __launch_bounds__(256, 2) k_force(ForceArgs a) {
+template <int T, bool ONE>
+__global__ void __launch_bounds__(256, 2) k_force64(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
-        // Frozen (a list overflowed earlier in this run): keep the state and
-        // mirror it into the output buffers so the buffer flip stays valid.
-        if (a.mode == MODE_FUSED) {
-            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.ns;
-                 t += (int64_t)gridDim.x * blockDim.x) {
-                a.sh_out[t] = a.sh_in[t];
-                for (int d = 0; d < 3; ++d) a.r_out[d * a.ns + t] = a.r_in[d * a.ns + t];
-            }
-        }
+        mirror_state(a);
         return;
     }
     __shared__ SmemTabs tb;
-    __shared__ __align__(16) float4 s_offf[MIXED ? kMaxWarps : 1][27];
-    __shared__ __align__(16) double s_offd[MIXED ? 1 : kMaxWarps][81];
-    const Pair &P = *a.pair;
-    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
-        tb.fe24[t] = P.fe24[t]; tb.fs2[t] = P.fs2[t]; tb.fe4[t] = P.fe4[t]; tb.fush[t] = P.fush[t];
-        tb.fc1[t] = P.fc1[t];
-        tb.de24[t] = P.e24[t]; tb.ds2[t] = P.s2[t]; tb.de4[t] = P.e4[t]; tb.dush[t] = P.ush[t];
-        if (t < MD_MAXT) { tb.dtm[t] = P.dtm[t]; tb.hdtm[t] = P.hdtm[t]; tb.mass[t] = P.mass[t]; }
-    }
+    __shared__ __align__(16) double s_offd[kMaxWarps][81];
+    load_tabs(*a.pair, tb);
     __syncthreads();
     const int64_t clock = a.fl->clock;
     const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
-    if (thermo) force_body<MIXED, T, ONE, true>(a, tb, s_offf, s_offd);
-    else force_body<MIXED, T, ONE, false>(a, tb, s_offf, s_offd);
-    // The last CTA to finish records which step the thermo partials describe
-    // and, in FUSED mode, advances the step clock (every CTA has read it).
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int prev = atomicAdd(a.done, 1u);
-        if (prev == gridDim.x - 1) {
-            *a.done = 0u;
-            a.fl->thermo = thermo ? 1u : 0u;
-            if (a.mode == MODE_FUSED) a.fl->clock = clock + 1;
-        }
-    }
+    if (thermo) force_body64<T, ONE, true>(a, tb, s_offd);
+    else force_body64<T, ONE, false>(a, tb, s_offd);
+    kernel_done(a, clock, thermo);
 }
 
 // v += dt/2 F/m; x += dt v; shadow refresh.  From a READY state.
@@ -947,11 +766,11 @@ __global__ void k_get_neighbors(const Box *__restrict__ boxes, const int32_t *__
 
 template <bool MIXED, int T, bool ONE>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
-    if (MIXED) {
+    if constexpr (MIXED) {
         // 2, 4 or 8 warps per CTA, each with a double buffer of R list rows.
         const int block = c->block;
         const int warps = block / 32;
-        const size_t smem = MD_FORCE_LIST == 1 ? 0 : (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
+        const size_t smem = (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
         static size_t smem_set = 0, occ_smem = 0;
         static int occ = 0, occ_block = 0;
         if (smem > smem_set) {
@@ -974,24 +793,23 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
-        c->kernels += 1;
-        return cudaGetLastError();
+    } else {
+        static int grid_cache[9][2][9] = {};
+        int &g = grid_cache[T][ONE][(c->block / 32) & 7];
+        if (g == 0) {
+            int per = 0;
+            cudaError_t e =
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force64<T, ONE>, c->block, 0);
+            if (e != cudaSuccess) return e;
+            g = per > 0 ? per : 1;
+        }
+        const int64_t warps_per_block = c->block / 32;
+        int64_t grid = (int64_t)c->nsm * g;
+        const int64_t need = (a.nwt + warps_per_block - 1) / warps_per_block;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        k_force64<T, ONE><<<(unsigned)grid, c->block, 0, c->stream>>>(a);
     }
-    static int grid_cache[2][9][2][9] = {};
-    int &g = grid_cache[MIXED][T][ONE][(c->block / 32) & 7];
-    if (g == 0) {
-        int per = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force<MIXED, T, ONE>,
-                                                                       c->block, 0);
-        if (e != cudaSuccess) return e;
-        g = per > 0 ? per : 1;
-    }
-    const int64_t warps_per_block = c->block / 32;
-    int64_t grid = (int64_t)c->nsm * g;
-    const int64_t need = (a.nwt + warps_per_block - 1) / warps_per_block;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
-    k_force<MIXED, T, ONE><<<(unsigned)grid, c->block, 0, c->stream>>>(a);
     c->kernels += 1;
     return cudaGetLastError();
 }
@@ -1036,6 +854,7 @@ cudaError_t launch_force(md_ctx *c, int mode) {
     a.mode = mode;
     a.thermo_every = c->params.thermo_every;
     a.done = &c->dflags->done;
+    a.tx_extra = c->debug_tx_extra;
     cudaError_t e = c->params.precision == MD_MIXED ? launch_force_m<true>(c, a)
                                                     : launch_force_m<false>(c, a);
     if (e == cudaSuccess && mode == MODE_FUSED) c->pc ^= 1;
