@@ -223,9 +223,10 @@ cudaError_t launch_adjoint(md_ctx *c, const double *G_aos, double gE, double *dx
 size_t adjoint_scratch_doubles(md_ctx *c);
 // The list entry that pads rows: the dummy shadow slot ns (kept far from every
 // atom) with a zero offset; a pair evaluated against it is masked by rc.
-inline uint32_t sentinel_entry(const md_ctx *c) {
-    return (uint32_t)c->ns | (kCodeZero << MD_IDX_BITS);
+__host__ __device__ inline uint32_t sentinel_entry(int64_t ns) {
+    return (uint32_t)ns | (kCodeZero << MD_IDX_BITS);
 }
+inline uint32_t sentinel_entry(const md_ctx *c) { return sentinel_entry(c->ns); }
 cudaError_t fill_list_sentinel(md_ctx *c);
 // md_api.cu: record a message for md_last_error(NULL) and return s
 md_status set_global_error(md_status s, const std::string &msg);

@@ -2,14 +2,14 @@
 // List Creation": "traditional binning methods used in many MD applications
 // (Verlet lists)", stored in a dense padded format).
 //
-// One warp per cell, one lane per home atom.  The warp stages the candidates
-// of the cell's 27-cell stencil in its own shared-memory window (FP32
-// cell-local coordinates shifted by the stencil offset, so a candidate's
-// coordinate is relative to the home cell's centre); then every lane walks
-// the window in order -- all lanes read the same candidate, a broadcast -- and
-// appends accepted neighbors straight into its own row of the warp-transposed
-// padded list.  The list is pre-filled with the sentinel entry, so slots past
-// an atom's count need no write.
+// One warp per cell.  The warp stages the candidates of the cell's 27-cell
+// stencil in its own shared-memory window (FP32 cell-local coordinates shifted
+// by the stencil offset, so a candidate's coordinate is relative to the home
+// cell's centre); then, home atom by home atom, its 32 lanes test 32
+// candidates at a time and write the accepted ones, compacted by a ballot
+// prefix in candidate order, into the atom's row of the warp-transposed padded
+// list.  The list is pre-filled with the sentinel entry, so slots past an
+// atom's count need no write.
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
 // the nearest-image FP64 distance r^2 = (dx*dx + dy*dy) + dz*dz, every op
@@ -105,24 +105,25 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
     const int M = __shfl_sync(0xffffffffu, incl, 26);
     __syncwarp();
 
+    const unsigned below = (1u << lane) - 1u;  // lanes under this one
+    const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
+    // padding candidates of a window: far away, never accepted
+    const float4 far = make_float4(1e4f, 1e4f, 1e4f, __uint_as_float(sentinel_entry(a.ns)));
     for (int hb = 0; hb < hm; hb += 32) {
-        const int ha = hb + lane;
-        const bool active = ha < hm;
-        const int64_t i = h0 + (active ? ha : 0);
-        const float4 si = a.sh[i];
-        int cnt = 0;
-        // this lane's row: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
-        uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
-        uint32_t *wp = rowp;  // where entry cnt goes
+        const int nh = min(32, hm - hb);
+        const bool active = lane < nh;
+        const float4 sl = a.sh[h0 + hb + (active ? lane : 0)];  // this lane's home atom
+        int cnt_l = 0;                                          // and its row length so far
         for (int w0 = 0; w0 < M; w0 += kCand) {
             const int Mw = min(kCand, M - w0);
+            const int Mp = (Mw + 31) & ~31;
             __syncwarp();
             for (int s = 0; s < 27; ++s) {
-                const int lo = max(s_pref[w][s], w0), hi = min(s_pref[w][s + 1], w0 + Mw);
+                const int lo_s = max(s_pref[w][s], w0), hi_s = min(s_pref[w][s + 1], w0 + Mw);
                 const float ox = (float)(s % 3 - 1) * B.hf[0];
                 const float oy = (float)((s / 3) % 3 - 1) * B.hf[1];
                 const float oz = (float)(s / 9 - 1) * B.hf[2];
-                for (int g = lo + lane; g < hi; g += 32) {
+                for (int g = lo_s + lane; g < hi_s; g += 32) {
                     const int64_t j = s_start[w][s] + (g - s_pref[w][s]);
                     const float4 p = a.sh[j];
                     cand[w][g - w0] = make_float4(
@@ -130,36 +131,44 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
                         __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));
                 }
             }
+            for (int g = Mw + lane; g < Mp; g += 32) cand[w][g] = far;
             __syncwarp();
-            if (active) {
-                const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
+            // Home atom by home atom: the lanes test 32 candidates at a time and
+            // the accepted ones go to the atom's row in candidate order (ballot
+            // prefix), so the row is the same as a sequential walk would give.
+            for (int hh = 0; hh < nh; ++hh) {
+                const float sx = __shfl_sync(0xffffffffu, sl.x, hh);
+                const float sy = __shfl_sync(0xffffffffu, sl.y, hh);
+                const float sz = __shfl_sync(0xffffffffu, sl.z, hh);
+                const int64_t i = h0 + hb + hh;
                 const uint32_t self = (uint32_t)i;
-#pragma unroll 4
-                for (int k = 0; k < Mw; ++k) {
-                    const float4 p = cand[w][k];
-                    const float dx = p.x - si.x, dy = p.y - si.y, dz = p.z - si.z;
+                int cnt = __shfl_sync(0xffffffffu, cnt_l, hh);
+                // row of atom i: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
+                uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
+                for (int g0 = 0; g0 < Mp; g0 += 32) {
+                    const float4 p = cand[w][g0 + lane];
+                    const float dx = p.x - sx, dy = p.y - sy, dz = p.z - sz;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if (r2 <= hi) {
-                        const uint32_t meta = __float_as_uint(p.w);
-                        bool acc = (meta & MD_IDX_MASK) != self;
-                        if (acc && r2 >= lo)   // rare: the exact FP64 decision
-                            acc = exact_test(a, B, i, meta & MD_IDX_MASK, dx, dy, dz);
-                        if (acc) {
-                            if (cnt < a.pad) *wp = meta;
-                            // next slot of the row: +1 within a group of T, else the next row
-                            wp += (cnt % T == T - 1) ? (33 - T) : 1;
-                            ++cnt;
-                        }
+                    const uint32_t meta = __float_as_uint(p.w);
+                    bool acc = r2 <= hi && (meta & MD_IDX_MASK) != self;
+                    if (acc && r2 >= lo)  // rare: the exact FP64 decision
+                        acc = exact_test(a, B, i, meta & MD_IDX_MASK, dx, dy, dz);
+                    const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                    if (acc) {
+                        const int k = cnt + __popc(bal & below);
+                        if (k < a.pad) rowp[(k / T) * 32 + k % T] = meta;
                     }
+                    cnt += __popc(bal);
                 }
+                if (lane == hh) cnt_l = cnt;
             }
         }
         if (active) {
-            a.nn[i] = cnt;
-            if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
+            a.nn[h0 + hb + lane] = cnt_l;
+            if (cnt_l > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
         }
-        const int mx = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
-        const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt : 0u);
+        const int mx = __reduce_max_sync(0xffffffffu, active ? cnt_l : 0);
+        const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt_l : 0u);
         if (lane == 0) {
             atomicMax(&a.fl->maxnn, mx);
             atomicAdd(&a.fl->sumnn, (unsigned long long)sm);
