@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kWarps = 4;       // cells per CTA (one warp each)
 constexpr int kCand = 640;      // candidates staged per warp per window
+constexpr int kU = 4;           // 32-candidate chunks tested per step
 
 struct BuildArgs {
     const Box *boxes;
@@ -145,20 +146,44 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
                 int cnt = __shfl_sync(0xffffffffu, cnt_l, hh);
                 // row of atom i: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
                 uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
-                for (int g0 = 0; g0 < Mp; g0 += 32) {
-                    const float4 p = cand[w][g0 + lane];
-                    const float dx = p.x - sx, dy = p.y - sy, dz = p.z - sz;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const uint32_t meta = __float_as_uint(p.w);
-                    bool acc = r2 <= hi && (meta & MD_IDX_MASK) != self;
-                    if (acc && r2 >= lo)  // rare: the exact FP64 decision
-                        acc = exact_test(a, B, i, meta & MD_IDX_MASK, dx, dy, dz);
-                    const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                    if (acc) {
-                        const int k = cnt + __popc(bal & below);
-                        if (k < a.pad) rowp[(k / T) * 32 + k % T] = meta;
+                // kU chunks of 32 candidates per step: their loads and tests
+                // are independent; only the row counter chains them
+                for (int g0 = 0; g0 < Mp; g0 += 32 * kU) {
+                    float4 p[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u)
+                        p[u] = g0 + 32 * u < Mp ? cand[w][g0 + 32 * u + lane] : far;
+                    bool acc[kU], band[kU];
+                    bool any_band = false;
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const float dx = p[u].x - sx, dy = p[u].y - sy, dz = p[u].z - sz;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const bool other = (__float_as_uint(p[u].w) & MD_IDX_MASK) != self;
+                        acc[u] = r2 < lo && other;
+                        band[u] = r2 >= lo && r2 <= hi && other;
+                        any_band |= band[u];
                     }
-                    cnt += __popc(bal);
+                    if (__any_sync(0xffffffffu, any_band)) {
+                        // rare: candidates near rs^2 take the exact FP64 decision
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            if (band[u]) {
+                                const float dx = p[u].x - sx, dy = p[u].y - sy, dz = p[u].z - sz;
+                                acc[u] = exact_test(a, B, i, __float_as_uint(p[u].w) & MD_IDX_MASK,
+                                                    dx, dy, dz);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const unsigned bal = __ballot_sync(0xffffffffu, acc[u]);
+                        if (acc[u]) {
+                            const int k = cnt + __popc(bal & below);
+                            if (k < a.pad) rowp[(k / T) * 32 + k % T] = __float_as_uint(p[u].w);
+                        }
+                        cnt += __popc(bal);
+                    }
                 }
                 if (lane == hh) cnt_l = cnt;
             }
