@@ -5,11 +5,13 @@
 // One warp per cell.  The warp stages the candidates of the cell's 27-cell
 // stencil in its own shared-memory window (FP32 cell-local coordinates shifted
 // by the stencil offset, so a candidate's coordinate is relative to the home
-// cell's centre); then, home atom by home atom, its 32 lanes test 32
-// candidates at a time and write the accepted ones, compacted by a ballot
-// prefix in candidate order, into the atom's row of the warp-transposed padded
-// list.  The list is pre-filled with the sentinel entry, so slots past an
-// atom's count need no write.
+// cell's centre).  It then takes the window 32 candidates at a time: the lanes
+// hold one candidate each and test it against every home atom (a broadcast
+// read), one ballot per home atom, which lands in that atom's lane as a 32-bit
+// accept mask; each lane then writes its atom's accepted candidates, in
+// candidate order, into the atom's row of the warp-transposed padded list.  The
+// list is pre-filled with the sentinel entry, so slots past an atom's count
+// need no write.
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
 // the nearest-image FP64 distance r^2 = (dx*dx + dy*dy) + dz*dz, every op
@@ -31,7 +33,6 @@ namespace {
 
 constexpr int kWarps = 4;       // cells per CTA (one warp each)
 constexpr int kCand = 640;      // candidates staged per warp per window
-constexpr int kU = 4;           // 32-candidate chunks tested per step
 
 struct BuildArgs {
     const Box *boxes;
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
     __shared__ __align__(16) float4 cand[kWarps][kCand];
     __shared__ int64_t s_start[kWarps][27];
     __shared__ int32_t s_pref[kWarps][28];
+    __shared__ __align__(16) float4 hpos[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * kWarps + w;
     if (c >= a.ncell) return;  // whole warp
@@ -106,15 +108,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
     const int M = __shfl_sync(0xffffffffu, incl, 26);
     __syncwarp();
 
-    const unsigned below = (1u << lane) - 1u;  // lanes under this one
+    // candidate index of the home cell's first atom (stencil slot 13 is the
+    // home cell itself)
+    const int self0 = s_pref[w][13];
     const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
     // padding candidates of a window: far away, never accepted
     const float4 far = make_float4(1e4f, 1e4f, 1e4f, __uint_as_float(sentinel_entry(a.ns)));
     for (int hb = 0; hb < hm; hb += 32) {
         const int nh = min(32, hm - hb);
         const bool active = lane < nh;
-        const float4 sl = a.sh[h0 + hb + (active ? lane : 0)];  // this lane's home atom
-        int cnt_l = 0;                                          // and its row length so far
+        const int64_t i = h0 + hb + (active ? lane : 0);  // this lane's home atom
+        const float4 si = a.sh[i];
+        __syncwarp();
+        hpos[w][lane] = si;
+        // row of atom i: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
+        uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
+        int cnt = 0;
         for (int w0 = 0; w0 < M; w0 += kCand) {
             const int Mw = min(kCand, M - w0);
             const int Mp = (Mw + 31) & ~31;
@@ -134,66 +143,54 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
             }
             for (int g = Mw + lane; g < Mp; g += 32) cand[w][g] = far;
             __syncwarp();
-            // Home atom by home atom: the lanes test 32 candidates at a time and
-            // the accepted ones go to the atom's row in candidate order (ballot
-            // prefix), so the row is the same as a sequential walk would give.
-            for (int hh = 0; hh < nh; ++hh) {
-                const float sx = __shfl_sync(0xffffffffu, sl.x, hh);
-                const float sy = __shfl_sync(0xffffffffu, sl.y, hh);
-                const float sz = __shfl_sync(0xffffffffu, sl.z, hh);
-                const int64_t i = h0 + hb + hh;
-                const uint32_t self = (uint32_t)i;
-                int cnt = __shfl_sync(0xffffffffu, cnt_l, hh);
-                // row of atom i: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
-                uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
-                // kU chunks of 32 candidates per step: their loads and tests
-                // are independent; only the row counter chains them
-                for (int g0 = 0; g0 < Mp; g0 += 32 * kU) {
-                    float4 p[kU];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u)
-                        p[u] = g0 + 32 * u < Mp ? cand[w][g0 + 32 * u + lane] : far;
-                    bool acc[kU], band[kU];
-                    bool any_band = false;
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) {
-                        const float dx = p[u].x - sx, dy = p[u].y - sy, dz = p[u].z - sz;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const bool other = (__float_as_uint(p[u].w) & MD_IDX_MASK) != self;
-                        acc[u] = r2 < lo && other;
-                        band[u] = r2 >= lo && r2 <= hi && other;
-                        any_band |= band[u];
-                    }
-                    if (__any_sync(0xffffffffu, any_band)) {
-                        // rare: candidates near rs^2 take the exact FP64 decision
-#pragma unroll
-                        for (int u = 0; u < kU; ++u) {
-                            if (band[u]) {
-                                const float dx = p[u].x - sx, dy = p[u].y - sy, dz = p[u].z - sz;
-                                acc[u] = exact_test(a, B, i, __float_as_uint(p[u].w) & MD_IDX_MASK,
-                                                    dx, dy, dz);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) {
-                        const unsigned bal = __ballot_sync(0xffffffffu, acc[u]);
-                        if (acc[u]) {
-                            const int k = cnt + __popc(bal & below);
-                            if (k < a.pad) rowp[(k / T) * 32 + k % T] = __float_as_uint(p[u].w);
-                        }
-                        cnt += __popc(bal);
+            for (int g0 = 0; g0 < Mp; g0 += 32) {
+                // Test phase: lane = candidate g0 + lane against every home atom;
+                // the ballots of home atom hh land in lane hh.
+                const float4 cl = cand[w][g0 + lane];
+                unsigned m_hi = 0u, m_lo = 0u;
+#pragma unroll 2
+                for (int hh = 0; hh < nh; ++hh) {
+                    const float4 h = hpos[w][hh];
+                    const float dx = cl.x - h.x, dy = cl.y - h.y, dz = cl.z - h.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const unsigned bh = __ballot_sync(0xffffffffu, r2 <= hi);
+                    const unsigned bl = __ballot_sync(0xffffffffu, r2 < lo);
+                    if (lane == hh) {
+                        m_hi = bh;
+                        m_lo = bl;
                     }
                 }
-                if (lane == hh) cnt_l = cnt;
+                if (!active) continue;
+                // Write phase: this lane's accepted candidates of the chunk, in
+                // candidate order, into its atom's row.
+                unsigned acc = m_lo, band = m_hi & ~m_lo;
+                const int gs = self0 + hb + lane - w0 - g0;  // the atom itself
+                if ((unsigned)gs < 32u) {
+                    acc &= ~(1u << gs);
+                    band &= ~(1u << gs);
+                }
+                while (band) {  // rare: candidates near rs^2 take the exact FP64 decision
+                    const int k = __ffs(band) - 1;
+                    band &= band - 1u;
+                    const float4 p = cand[w][g0 + k];
+                    if (exact_test(a, B, i, __float_as_uint(p.w) & MD_IDX_MASK, p.x - si.x,
+                                   p.y - si.y, p.z - si.z))
+                        acc |= 1u << k;
+                }
+                while (acc) {
+                    const int k = __ffs(acc) - 1;
+                    acc &= acc - 1u;
+                    if (cnt < a.pad) rowp[(cnt / T) * 32 + cnt % T] = __float_as_uint(cand[w][g0 + k].w);
+                    ++cnt;
+                }
             }
         }
         if (active) {
-            a.nn[h0 + hb + lane] = cnt_l;
-            if (cnt_l > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
+            a.nn[i] = cnt;
+            if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
         }
-        const int mx = __reduce_max_sync(0xffffffffu, active ? cnt_l : 0);
-        const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt_l : 0u);
+        const int mx = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
+        const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt : 0u);
         if (lane == 0) {
             atomicMax(&a.fl->maxnn, mx);
             atomicAdd(&a.fl->sumnn, (unsigned long long)sm);
