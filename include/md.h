@@ -127,9 +127,10 @@ md_status md_bin_sort(md_ctx *ctx);
  * atom i, every j != i whose nearest-image distance satisfies
  *   r^2 = (dx*dx + dy*dy) + dz*dz < (rc + skin)^2,  d = x_j - x_i folded once by +-L,
  * evaluated in FP64 with each operation rounded separately, searched over the
- * 27 cells around i's cell.  The list is stored padded and transposed
- * (warp-coalesced).  Returns MD_ERR_NEIGH_OVERFLOW if a row needs more than
- * the current pad (the pad is then grown, call again). */
+ * 27 cells around i's cell.  If the atoms moved since the last cell sort, it
+ * first re-sorts them (as md_bin_sort).  The list is stored padded and
+ * transposed (warp-coalesced).  Returns MD_ERR_NEIGH_OVERFLOW if a row needs
+ * more than the current pad (the pad is then grown, call again). */
 md_status md_build_neighbors(md_ctx *ctx);
 
 /* Lennard-Jones 12-6 forces and energy over the current list (Section

@@ -118,7 +118,7 @@ md_status setup_pair(md_ctx *c, const double *eps, const double *sigma) {
     P.half_skin = 0.5 * p.skin;
     P.rc2f = (float)P.rc2;
     P.rs2f = (float)P.rs2;
-    P.bandf = (float)(1e-3 * P.rs2);
+    P.bandf = (float)(3e-5 * P.rs2);  // > 20x the FP32 r^2 error bound (md_neigh.cu)
     c->eps.assign(eps, eps + nt * nt);
     c->sigma.assign(sigma, sigma + nt * nt);
     for (int a = 0; a < nt; ++a)
@@ -201,7 +201,7 @@ md_status build_with_retry(md_ctx *c) {
 
 md_status sort_build_forces(md_ctx *c, bool raw) {
     CK(launch_bin_sort(c, raw));
-    c->sorted = true;
+    c->sorted_at = c->step;
     c->built_at = c->step;
     md_status s = build_with_retry(c);
     if (s) return s;
@@ -510,7 +510,7 @@ md_status md_bin_sort(md_ctx *c) {
     if (s) return s;
     if (c->hflags->status & ST_TIMEOUT) return timeout_fail(c);
     if (c->hflags->status & ST_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position");
-    c->sorted = true;
+    c->sorted_at = c->step;
     c->built_at = -1;
     c->list_valid = false;
     c->forces_valid = false;
@@ -520,6 +520,12 @@ md_status md_bin_sort(md_ctx *c) {
 
 md_status md_build_neighbors(md_ctx *c) {
     if (!c) return MD_ERR_ARG;
+    if (c->sorted_at != c->step) {
+        // the atoms moved since their cells were assigned: re-sort first, so
+        // every neighbor lies in the 27 cells around an atom's cell
+        md_status s = md_bin_sort(c);
+        if (s) return s;
+    }
     CK(launch_build(c));
     md_status s = read_flags(c);
     if (s) return s;
@@ -660,6 +666,7 @@ md_status md_step(md_ctx *c, int32_t nsteps, md_thermo *last_out) {
                 c->list_valid) {
                 s = run_period_graph(c);
                 if (s) return s;
+                c->sorted_at = n;
                 c->built_at = n;
                 n += every;
                 continue;
@@ -667,6 +674,7 @@ md_status md_step(md_ctx *c, int32_t nsteps, md_thermo *last_out) {
             if (n % every == 0 && c->built_at != n) {
                 CK(launch_bin_sort(c, false));
                 CK(launch_build(c));
+                c->sorted_at = n;
                 c->built_at = n;
                 c->list_valid = true;
             }
@@ -818,7 +826,7 @@ md_status md_force_backward(md_ctx *c, const double *dL_dF, double dL_dE, double
     if (!c->ready) return fail(c, MD_ERR_ARG, "internal: state between half-steps");
     // The list is recomputed from the current positions, never reused.
     CK(launch_bin_sort(c, false));
-    c->sorted = true;
+    c->sorted_at = c->step;
     c->list_valid = false;
     c->forces_valid = false;
     invalidate_graphs(c);

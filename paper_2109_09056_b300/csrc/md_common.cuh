@@ -173,7 +173,8 @@ struct md_ctx {
     int pc = 0, oc = 0;            // current position / order buffers
     int64_t step = 0;
     bool ready = true;             // READY: v = v_n and f = F(x_n); else DRIFTED
-    bool list_valid = false, sorted = false;
+    bool list_valid = false;
+    int64_t sorted_at = -1;        // step of the state at the last cell sort
     int64_t host_builds = 0;
     int32_t cur_tlog_rows = 0;
 

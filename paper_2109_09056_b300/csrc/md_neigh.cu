@@ -15,12 +15,15 @@
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
 // the nearest-image FP64 distance r^2 = (dx*dx + dy*dy) + dz*dz, every op
-// rounded separately, is < (rc+skin)^2.  The FP32 r^2 of the staged
-// coordinates differs from it by < 2e-5 (|coords| <= 1.5 h, h <= 4.2; each
-// coordinate carries <= 2^-24 relative rounding), so candidates with FP32 r^2
-// outside [rs^2 - band, rs^2 + band], band = 1e-3 rs^2, are decided in FP32
-// and the few inside the band are re-tested with the exact FP64 rule on the
-// wrapped FP64 positions.  When an axis has only 2 cells, the -1 and +1 stencil
+// rounded separately, is < (rc+skin)^2 = rs^2.  The FP32 r^2 of the staged
+// coordinates differs from it by less than 1.5e-6 rs^2: with u = 2^-24, cell
+// edge h < 1.5 rs and shadows refreshed at the sort (|shadow| <= h/2), a
+// component of d carries at most u (h/2 + h + 1.5 h + h/2 + rs) <= 6.25 u rs
+// (the two shadows, the FP32 cell edge, the shifted candidate, the
+// difference), so r^2 near rs^2 is off by at most 2 sqrt(3) rs 6.25 u rs plus
+// two FP32 roundings of r^2, < 24 u rs^2.  Candidates with FP32 r^2 outside
+// [rs^2 - band, rs^2 + band], band = 3e-5 rs^2, are decided in FP32; the few
+// inside are re-tested with the exact FP64 rule on the wrapped FP64 positions.  When an axis has only 2 cells, the -1 and +1 stencil
 // slots hold the same cell under two images; only one image can lie within
 // rs (L > 2 rs), and the FP64 re-test checks that the slot's image is the
 // nearest one.
@@ -180,7 +183,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
                 while (acc) {
                     const int k = __ffs(acc) - 1;
                     acc &= acc - 1u;
-                    if (cnt < a.pad) rowp[(cnt / T) * 32 + cnt % T] = __float_as_uint(cand[w][g0 + k].w);
+                    const unsigned uc = (unsigned)cnt;
+                    if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = __float_as_uint(cand[w][g0 + k].w);
                     ++cnt;
                 }
             }

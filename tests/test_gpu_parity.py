@@ -85,6 +85,24 @@ def test_shifted_energy():
     assert sysm.compute_forces() == pytest.approx(pe_o, rel=1e-12)
 
 
+def test_build_after_steps_resorts_first():
+    """md_build_neighbors on a drifted state re-sorts before building: the
+    permutation and the lists equal the oracle's sort and list of the snapshot."""
+    s = mi.lj_melt(10, seed=12)
+    sysm = make(s, "mixed")
+    sysm.step(27)                        # rebuilt at 20; drifted since
+    st = sysm.state(forces=False)
+    x_int = st["x"][st["ids"]]
+    sysm.build_neighbors()               # no explicit bin_sort
+    perm_o, xs_o, _ = oracle.bin_sort(x_int, s.box, RS)
+    assert np.array_equal(sysm.permutation(), perm_o)
+    nn, rows = sysm.neighbors()
+    nn_o, rows_o = oracle.neighbors(xs_o, s.box, RS)
+    assert np.array_equal(nn, nn_o)
+    for k in range(len(nn)):
+        assert set(rows[k, : nn[k]].tolist()) == set(rows_o[k, : nn_o[k]].tolist())
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_resort_and_list_after_steps_on_gpu_snapshot(precision):
     """Per-stage parity on the GPU's own state: run, snapshot, then the GPU's
