@@ -5,13 +5,14 @@
 // One warp per cell.  The warp stages the candidates of the cell's 27-cell
 // stencil in its own shared-memory window (FP32 cell-local coordinates shifted
 // by the stencil offset, so a candidate's coordinate is relative to the home
-// cell's centre).  It then takes the window 32 candidates at a time: the lanes
-// hold one candidate each and test it against every home atom (a broadcast
-// read), one ballot per home atom, which lands in that atom's lane as a 32-bit
-// accept mask; each lane then writes its atom's accepted candidates, in
-// candidate order, into the atom's row of the warp-transposed padded list.  The
-// list is pre-filled with the sentinel entry, so slots past an atom's count
-// need no write.
+// cell's centre), leaving out those farther than rs from the whole home cell
+// (about a quarter of them).  It then takes the window 64 candidates at a
+// time: each lane holds two and tests them against every home atom (a
+// broadcast read), one ballot per home atom and candidate half, which lands in
+// that atom's lane as a 32-bit accept mask; each lane then writes its atom's
+// accepted candidates, in candidate order, into the atom's row of the
+// warp-transposed padded list.  The list is pre-filled with the sentinel
+// entry, so slots past an atom's count need no write.
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
 // the nearest-image FP64 distance r^2 = (dx*dx + dy*dy) + dz*dz, every op
@@ -111,82 +112,104 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
     const int M = __shfl_sync(0xffffffffu, incl, 26);
     __syncwarp();
 
-    // candidate index of the home cell's first atom (stencil slot 13 is the
-    // home cell itself)
-    const int self0 = s_pref[w][13];
     const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
     // padding candidates of a window: far away, never accepted
     const float4 far = make_float4(1e4f, 1e4f, 1e4f, __uint_as_float(sentinel_entry(a.ns)));
+    // A candidate farther than rs from every point of the home cell cannot be
+    // a neighbor of any home atom and is not staged (a 1e-4 relative margin
+    // covers the FP32 rounding of the coordinates).
+    const float ex_h = 0.5f * B.hf[0] * 1.0001f, ey_h = 0.5f * B.hf[1] * 1.0001f,
+                ez_h = 0.5f * B.hf[2] * 1.0001f;
+    const float cull2 = a.rs2f * 1.0002f;
+    const unsigned below = (1u << lane) - 1u;
     for (int hb = 0; hb < hm; hb += 32) {
         const int nh = min(32, hm - hb);
         const bool active = lane < nh;
         const int64_t i = h0 + hb + (active ? lane : 0);  // this lane's home atom
+        const uint32_t self_meta = (uint32_t)i | (kCodeZero << MD_IDX_BITS);
         const float4 si = a.sh[i];
         __syncwarp();
         hpos[w][lane] = si;
         // row of atom i: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
         uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
         int cnt = 0;
+        // this lane's accepted candidates among window slots [gb, gb + 32), in
+        // candidate order, into its atom's row (the atom itself skipped)
+        auto write_chunk = [&](int gb, unsigned m_hi, unsigned m_lo) {
+            unsigned acc = m_lo, band = m_hi & ~m_lo;
+            while (band) {  // rare: candidates near rs^2 take the exact FP64 decision
+                const int k = __ffs(band) - 1;
+                band &= band - 1u;
+                const float4 p = cand[w][gb + k];
+                const uint32_t meta = __float_as_uint(p.w);
+                if (meta != self_meta &&
+                    exact_test(a, B, i, meta & MD_IDX_MASK, p.x - si.x, p.y - si.y, p.z - si.z))
+                    acc |= 1u << k;
+            }
+            while (acc) {
+                const int k = __ffs(acc) - 1;
+                acc &= acc - 1u;
+                const uint32_t meta = __float_as_uint(cand[w][gb + k].w);
+                if (meta != self_meta) {
+                    const unsigned uc = (unsigned)cnt;
+                    if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = meta;
+                    ++cnt;
+                }
+            }
+        };
         for (int w0 = 0; w0 < M; w0 += kCand) {
             const int Mw = min(kCand, M - w0);
-            const int Mp = (Mw + 31) & ~31;
             __syncwarp();
+            int mc = 0;  // candidates of this window kept in cand[w]
             for (int s = 0; s < 27; ++s) {
                 const int lo_s = max(s_pref[w][s], w0), hi_s = min(s_pref[w][s + 1], w0 + Mw);
                 const float ox = (float)(s % 3 - 1) * B.hf[0];
                 const float oy = (float)((s / 3) % 3 - 1) * B.hf[1];
                 const float oz = (float)(s / 9 - 1) * B.hf[2];
-                for (int g = lo_s + lane; g < hi_s; g += 32) {
-                    const int64_t j = s_start[w][s] + (g - s_pref[w][s]);
-                    const float4 p = a.sh[j];
-                    cand[w][g - w0] = make_float4(
-                        p.x + ox, p.y + oy, p.z + oz,
-                        __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));
+                for (int gs = lo_s; gs < hi_s; gs += 32) {
+                    const int g = gs + lane;
+                    bool keep = false;
+                    float4 q = far;
+                    if (g < hi_s) {
+                        const int64_t j = s_start[w][s] + (g - s_pref[w][s]);
+                        const float4 p = a.sh[j];
+                        q = make_float4(p.x + ox, p.y + oy, p.z + oz,
+                                        __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));
+                        const float ex = fmaxf(fabsf(q.x) - ex_h, 0.f);
+                        const float ey = fmaxf(fabsf(q.y) - ey_h, 0.f);
+                        const float ez = fmaxf(fabsf(q.z) - ez_h, 0.f);
+                        keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < cull2;
+                    }
+                    const unsigned bk = __ballot_sync(0xffffffffu, keep);
+                    if (keep) cand[w][mc + __popc(bk & below)] = q;
+                    mc += __popc(bk);
                 }
             }
-            for (int g = Mw + lane; g < Mp; g += 32) cand[w][g] = far;
+            const int Mp = (mc + 63) & ~63;  // kCand is a multiple of 64
+            for (int g = mc + lane; g < Mp; g += 32) cand[w][g] = far;
             __syncwarp();
-            for (int g0 = 0; g0 < Mp; g0 += 32) {
-                // Test phase: lane = candidate g0 + lane against every home atom;
-                // the ballots of home atom hh land in lane hh.
-                const float4 cl = cand[w][g0 + lane];
-                unsigned m_hi = 0u, m_lo = 0u;
-#pragma unroll 2
+            for (int g0 = 0; g0 < Mp; g0 += 64) {
+                // Test phase: lane = candidates g0 + lane and g0 + 32 + lane
+                // against every home atom; home atom hh's ballots land in lane hh.
+                const float4 c0 = cand[w][g0 + lane], c1 = cand[w][g0 + 32 + lane];
+                unsigned hi0 = 0u, lo0 = 0u, hi1 = 0u, lo1 = 0u;
                 for (int hh = 0; hh < nh; ++hh) {
                     const float4 h = hpos[w][hh];
-                    const float dx = cl.x - h.x, dy = cl.y - h.y, dz = cl.z - h.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const unsigned bh = __ballot_sync(0xffffffffu, r2 <= hi);
-                    const unsigned bl = __ballot_sync(0xffffffffu, r2 < lo);
+                    const float dx0 = c0.x - h.x, dy0 = c0.y - h.y, dz0 = c0.z - h.z;
+                    const float dx1 = c1.x - h.x, dy1 = c1.y - h.y, dz1 = c1.z - h.z;
+                    const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
+                    const float r21 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
+                    const unsigned bh0 = __ballot_sync(0xffffffffu, r20 <= hi);
+                    const unsigned bl0 = __ballot_sync(0xffffffffu, r20 < lo);
+                    const unsigned bh1 = __ballot_sync(0xffffffffu, r21 <= hi);
+                    const unsigned bl1 = __ballot_sync(0xffffffffu, r21 < lo);
                     if (lane == hh) {
-                        m_hi = bh;
-                        m_lo = bl;
+                        hi0 = bh0; lo0 = bl0; hi1 = bh1; lo1 = bl1;
                     }
                 }
                 if (!active) continue;
-                // Write phase: this lane's accepted candidates of the chunk, in
-                // candidate order, into its atom's row.
-                unsigned acc = m_lo, band = m_hi & ~m_lo;
-                const int gs = self0 + hb + lane - w0 - g0;  // the atom itself
-                if ((unsigned)gs < 32u) {
-                    acc &= ~(1u << gs);
-                    band &= ~(1u << gs);
-                }
-                while (band) {  // rare: candidates near rs^2 take the exact FP64 decision
-                    const int k = __ffs(band) - 1;
-                    band &= band - 1u;
-                    const float4 p = cand[w][g0 + k];
-                    if (exact_test(a, B, i, __float_as_uint(p.w) & MD_IDX_MASK, p.x - si.x,
-                                   p.y - si.y, p.z - si.z))
-                        acc |= 1u << k;
-                }
-                while (acc) {
-                    const int k = __ffs(acc) - 1;
-                    acc &= acc - 1u;
-                    const unsigned uc = (unsigned)cnt;
-                    if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = __float_as_uint(cand[w][g0 + k].w);
-                    ++cnt;
-                }
+                write_chunk(g0, hi0, lo0);
+                write_chunk(g0 + 32, hi1, lo1);
             }
         }
         if (active) {
