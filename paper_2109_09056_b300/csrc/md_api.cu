@@ -66,7 +66,7 @@ void free_all(md_ctx *c) {
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
     F(c->tpart); F(c->tbox); F(c->fpart); F(c->tlog); F(c->dscratch); F(c->stage);
-    F(c->restage);
+    F(c->restage); F(c->scan_part);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -350,6 +350,7 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     CK(dalloc(&c->count, (size_t)c->ncell_tot));
     CK(cudaMemset(c->count, 0, (size_t)c->ncell_tot * sizeof(int32_t)));
     CK(dalloc(&c->cstart, (size_t)c->ncell_tot + 1));
+    CK(dalloc(&c->scan_part, (size_t)c->ncell_tot / 1024 + 1));
     CK(dalloc(&c->dbox, (size_t)nbox));
     CK(cudaMemcpy(c->dbox, c->hbox.data(), sizeof(Box) * nbox, cudaMemcpyHostToDevice));
     std::vector<int32_t> tb(ns / 32), cb((size_t)c->ncell_tot);

@@ -150,6 +150,7 @@ struct md_ctx {
     int32_t *img[2] = {nullptr, nullptr}, *cellc[2] = {nullptr, nullptr};
     int32_t *cell = nullptr, *rank = nullptr, *perm = nullptr, *ptmp = nullptr;
     int32_t *count = nullptr, *cstart = nullptr, *nn = nullptr;
+    int32_t *scan_part = nullptr;  // per-block sums of the cell-count scan
     uint32_t *nbr = nullptr;
     size_t nbr_words = 0;
     mdb::Box *dbox = nullptr;

@@ -11,8 +11,9 @@
 // broadcast read), one ballot per home atom and candidate half, which lands in
 // that atom's lane as a 32-bit accept mask; each lane then writes its atom's
 // accepted candidates, in candidate order, into the atom's row of the
-// warp-transposed padded list.  The list is pre-filled with the sentinel
-// entry, so slots past an atom's count need no write.
+// warp-transposed padded list, then the sentinel entry into the row's
+// remaining slots (the rows of padding slots hold it from the list's
+// allocation on).
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
 // the nearest-image FP64 distance r^2 = (dx*dx + dy*dy) + dz*dz, every op
@@ -215,6 +216,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
         if (active) {
             a.nn[i] = cnt;
             if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
+            // the row's slots past its count hold the sentinel entry
+            const uint32_t sent = sentinel_entry(a.ns);
+            for (unsigned k = (unsigned)cnt; k < (unsigned)a.pad; ++k)
+                rowp[(k / T) * 32u + k % T] = sent;
         }
         const int mx = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
         const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt : 0u);
@@ -240,8 +245,9 @@ cudaError_t launch_build_t(md_ctx *c, const BuildArgs &a) {
 
 }  // namespace
 
-// Every list slot (including the rows of padding slots, which no build
-// writes) holds the sentinel entry unless a build wrote a neighbor there.
+// At allocation every list slot gets the sentinel entry; the rows of padding
+// slots keep it (no build writes them), every build rewrites the rows of real
+// atoms in full.
 cudaError_t fill_list_sentinel(md_ctx *c) {
     const size_t words = (size_t)c->ns * c->pad;
     k_fill_u32<<<(unsigned)std::min<size_t>((words + 255) / 256, 65535), 256, 0, c->stream>>>(
@@ -269,9 +275,7 @@ cudaError_t launch_build(md_ctx *c) {
     a.nn = c->nn;
     a.nbr = c->nbr;
     a.fl = c->dflags;
-    // the previous list's rows are stale: every slot back to the sentinel
-    cudaError_t e = fill_list_sentinel(c);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     switch (c->T) {
         case 1: e = launch_build_t<1>(c, a); break;
         case 2: e = launch_build_t<2>(c, a); break;

@@ -5,8 +5,9 @@
 //
 //   k_bin      : x = O + r (or raw input), wrap into [0, L), cell id, atomic
 //                histogram; each atom takes a slot rank inside its cell.
-//   k_scan     : exclusive prefix sum of the per-cell counts (one CTA), plus the
-//                per-build bookkeeping (dangerous-build test, counter resets).
+//   k_scan_sum, k_scan_out : exclusive prefix sum of the per-cell counts
+//                (block sums, then per-block scans), plus the per-build
+//                bookkeeping (dangerous-build test, counter resets).
 //   k_scatter  : atom -> slot (cell start + atomic rank).
 //   k_segsort  : per cell, order the slots by prior index, which makes the
 //                permutation stable: new order = sort by (cell, prior index).
@@ -60,89 +61,141 @@ __global__ void k_bin(const Box *__restrict__ boxes, const int32_t *__restrict__
                       double *__restrict__ xw, int32_t *__restrict__ cell,
                       int32_t *__restrict__ rank, int32_t *__restrict__ count, Flags *fl) {
     if (fl->status & ST_FREEZE) return;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= ns) return;
-    const Box &B = boxes[tile_box[i >> 5]];
-    if (i - B.slot_off >= B.n) return;
-    double x[3];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool live = i < ns;
+    const Box &B = boxes[tile_box[(live ? i : 0) >> 5]];
+    live = live && i - B.slot_off < B.n;
     float disp2 = 0.f;
-    if (raw) {
-        for (int d = 0; d < 3; ++d) x[d] = xraw[d * ns + i];
-    } else {
-        int cc[3];
-        unpack_cell(cellc[i], cc[0], cc[1], cc[2]);
-        for (int d = 0; d < 3; ++d) {
-            double rd = r[d * ns + i];
-            x[d] = __dadd_rn(cell_centre(cc[d], B.h[d]), rd);
-            float dd = (float)(rd - rbuild[d * ns + i]);
-            disp2 += dd * dd;
+    int32_t gc = -1;
+    if (live) {
+        double x[3];
+        if (raw) {
+            for (int d = 0; d < 3; ++d) x[d] = xraw[d * ns + i];
+        } else {
+            int cc[3];
+            unpack_cell(cellc[i], cc[0], cc[1], cc[2]);
+            for (int d = 0; d < 3; ++d) {
+                const double rd = r[d * ns + i];
+                x[d] = __dadd_rn(cell_centre(cc[d], B.h[d]), rd);
+                const float dd = (float)(rd - rbuild[d * ns + i]);
+                disp2 += dd * dd;
+            }
+        }
+        if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) {
+            atomicOr(&fl->status, ST_NONFINITE);
+            live = false;
+        } else {
+            int c[3];
+            for (int d = 0; d < 3; ++d) {
+                const double L = B.L[d];
+                double w;
+                if (x[d] >= 0.0 && x[d] < L) {
+                    // inside the box: the general rule below gives w = x, k = 0
+                    // (x/L may round to 1, then w = (x - L) + L = x exactly);
+                    // + 0.0 maps -0.0 to +0.0 as it does
+                    w = __dadd_rn(x[d], 0.0);
+                } else {
+                    const double q = floor(__ddiv_rn(x[d], L));
+                    w = __dsub_rn(x[d], __dmul_rn(L, q));
+                    int k = (int)q;
+                    if (w < 0.0) { w = __dadd_rn(w, L); k -= 1; }
+                    if (w >= L) { w = __dsub_rn(w, L); k += 1; }
+                    img[d * ns + i] += k;
+                }
+                xw[d * ns + i] = w;
+                int cd = __double2int_rz(__dmul_rn(w, B.inv[d]));
+                cd = cd < 0 ? 0 : (cd > B.nc[d] - 1 ? B.nc[d] - 1 : cd);
+                c[d] = cd;
+            }
+            gc = B.cell_off + (c[2] * B.nc[1] + c[1]) * B.nc[0] + c[0];
         }
     }
-    bool finite = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
-    if (!finite) {
-        atomicOr(&fl->status, ST_NONFINITE);
-        return;
+    // Slot ranks inside each cell: one atomic per run of lanes with the same
+    // cell (atoms still in the previous cell order mostly share cells).
+    const unsigned grp = __match_any_sync(0xffffffffu, gc);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (live && lane == leader) base = atomicAdd(&count[gc], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (live) {
+        cell[i] = gc;
+        rank[i] = base + __popc(grp & ((1u << lane) - 1u));
     }
-    int c[3];
-    for (int d = 0; d < 3; ++d) {
-        const double L = B.L[d];
-        double q = floor(__ddiv_rn(x[d], L));
-        double p = __dmul_rn(L, q);
-        double w = __dsub_rn(x[d], p);
-        int k = (int)q;
-        if (w < 0.0) { w = __dadd_rn(w, L); k -= 1; }
-        if (w >= L) { w = __dsub_rn(w, L); k += 1; }
-        img[d * ns + i] += k;
-        xw[d * ns + i] = w;
-        int cd = __double2int_rz(__dmul_rn(w, B.inv[d]));
-        cd = cd < 0 ? 0 : (cd > B.nc[d] - 1 ? B.nc[d] - 1 : cd);
-        c[d] = cd;
+    if (!raw) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, live ? __float_as_uint(sqrtf(disp2)) : 0u);
+        if (lane == 0 && m != 0u) atomicMax(&fl->maxdisp_bits, m);
     }
-    int32_t gc = B.cell_off + (c[2] * B.nc[1] + c[1]) * B.nc[0] + c[0];
-    cell[i] = gc;
-    rank[i] = atomicAdd(&count[gc], 1);
-    if (!raw) atomicMax(&fl->maxdisp_bits, __float_as_uint(sqrtf(disp2)));
 }
 
-// One CTA of 1024 threads: exclusive scan of count[0..nc) into cstart[0..nc],
-// zeroing count for the next build.
-__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ count,
-                                               int32_t *__restrict__ cstart, int32_t ncell,
-                                               Flags *fl, double half_skin, int raw) {
+// Exclusive scan of count[0..ncell) into cstart[0..ncell] in two passes over
+// blocks of kScanCells cells: block sums, then each block adds the sums of
+// the blocks before it (in order) to its own scan.
+constexpr int kScanThreads = 256, kScanPer = 4, kScanCells = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sum(const int32_t *__restrict__ count,
+                                                           int32_t ncell, int32_t *__restrict__ part,
+                                                           const Flags *fl) {
     if (fl->status & ST_FREEZE) return;
-    __shared__ int32_t wsum[32];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int per = (ncell + 1023) / 1024;
-    const int lo = min(ncell, tid * per), hi = min(ncell, lo + per);
+    __shared__ int32_t red[kScanThreads / 32];
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * kScanCells;
     int32_t s = 0;
-    for (int c = lo; c < hi; ++c) s += count[c];
-    // block exclusive scan of s
+    for (int k = 0; k < kScanPer; ++k) {
+        const int c = c0 + k * kScanThreads + tid;
+        if (c < ncell) s += count[c];
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_out(const int32_t *__restrict__ count,
+                                                           int32_t *__restrict__ cstart,
+                                                           int32_t ncell,
+                                                           const int32_t *__restrict__ part,
+                                                           Flags *fl, double half_skin, int raw) {
+    if (fl->status & ST_FREEZE) return;
+    __shared__ int32_t wsum[kScanThreads / 32];
+    __shared__ int32_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // sums of the blocks before this one, in block order
+    if (w == 0) {
+        int32_t b = 0;
+        for (int k = lane; k < (int)blockIdx.x; k += 32) b += part[k];
+        b = __reduce_add_sync(0xffffffffu, b);
+        if (lane == 0) s_base = b;
+    }
+    // this thread's kScanPer consecutive cells
+    const int c0 = blockIdx.x * kScanCells + tid * kScanPer;
+    int32_t v[kScanPer];
+    int32_t s = 0;
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = c0 + k < ncell ? count[c0 + k] : 0;
+        s += v[k];
+    }
     int32_t incl = s;
     for (int o = 1; o < 32; o <<= 1) {
-        int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
     if (lane == 31) wsum[w] = incl;
     __syncthreads();
-    if (w == 0) {
-        int32_t ws = wsum[lane];
-        int32_t wi = ws;
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        wsum[lane] = wi - ws;
+    int32_t before = s_base;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    int32_t run = before + incl - s;
+    for (int k = 0; k < kScanPer; ++k) {
+        if (c0 + k < ncell) cstart[c0 + k] = run;
+        run += v[k];
     }
-    __syncthreads();
-    int32_t run = wsum[w] + incl - s;
-    for (int c = lo; c < hi; ++c) {
-        int32_t k = count[c];
-        cstart[c] = run;
-        run += k;
-        count[c] = 0;
-    }
-    if (tid == 1023) cstart[ncell] = wsum[31] + incl;
-    if (tid == 0) {
+    // the grid's last thread has summed every cell (zeros past ncell)
+    if (blockIdx.x == gridDim.x - 1 && tid == kScanThreads - 1) cstart[ncell] = run;
+    if (blockIdx.x == 0 && tid == 0) {
         if (!raw && __uint_as_float(fl->maxdisp_bits) > (float)half_skin) fl->dangerous += 1;
         fl->builds += 1;
         fl->maxdisp_bits = 0u;
@@ -271,8 +324,12 @@ cudaError_t launch_bin_sort(md_ctx *c, bool raw_input) {
     k_bin<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
         c->dbox, c->tile_box, c->ns, raw_input ? 1 : 0, c->r[pc], c->xraw, c->cellc[oc],
         c->img[oc], c->rbuild, c->xw, c->cell, c->rank, c->count, c->dflags);
-    k_scan<<<1, 1024, 0, c->stream>>>(c->count, c->cstart, c->ncell_tot, c->dflags,
-                                       c->hpair.half_skin, raw_input ? 1 : 0);
+    const unsigned nsb = blocks_for(c->ncell_tot, kScanCells);
+    k_scan_sum<<<nsb, kScanThreads, 0, c->stream>>>(c->count, c->ncell_tot, c->scan_part,
+                                                    c->dflags);
+    k_scan_out<<<nsb, kScanThreads, 0, c->stream>>>(c->count, c->cstart, c->ncell_tot,
+                                                    c->scan_part, c->dflags, c->hpair.half_skin,
+                                                    raw_input ? 1 : 0);
     k_scatter<<<blocks_for(c->ns, t), t, 0, c->stream>>>(c->dbox, c->tile_box, c->ns, c->cell,
                                                           c->rank, c->cstart, c->ptmp,
                                                           c->dflags);
@@ -283,7 +340,7 @@ cudaError_t launch_bin_sort(md_ctx *c, bool raw_input) {
         c->img[oc], c->r[pc], c->v[oc ^ 1], c->type[oc ^ 1], c->id[oc ^ 1], c->img[oc ^ 1],
         c->cellc[oc ^ 1], c->cellc[oc], c->sh[pc], c->rbuild, c->xws, c->nn, c->dflags);
     c->oc ^= 1;
-    c->kernels += 5;
+    c->kernels += 6;
     return cudaGetLastError();
 }
 
