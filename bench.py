@@ -28,6 +28,9 @@ import sys
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# the mixed force kernel's sources (the traffic record is keyed by their hash)
+FORCE_SOURCES = [os.path.join(ROOT, "paper_2109_09056_b300", "csrc", f)
+                 for f in ("md_force.cu", "md_common.cuh")]
 sys.path.insert(0, ROOT)
 
 METRIC = "atom-steps/s LJ 4M atoms, mixed vs FP64 on 1 B300; pair-force % of roofline"
@@ -133,15 +136,21 @@ def peaks():
         return {}
 
 
-def traffic_record(kernel_file: str):
+def kernel_sources_sha256(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def traffic_record(kernel_files):
     """DRAM bytes per launch of the force kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    valid only while the kernel's sources are unchanged since the capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "force_kernel_traffic.json")))
     except (OSError, ValueError):
         return None
-    sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-    return rec if rec.get("kernel_sha256") == sha else None
+    return rec if rec.get("kernel_sha256") == kernel_sources_sha256(kernel_files) else None
 
 
 def oracle_sample(sysd):
@@ -307,7 +316,7 @@ def run_ours(args, dist):
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6400.0
     achieved = alg_bytes / t_launch / 1e9
-    rec = traffic_record(os.path.join(ROOT, "paper_2109_09056_b300", "csrc", "md_force.cu"))
+    rec = traffic_record(FORCE_SOURCES)
     traffic = rec["dram_bytes_per_launch"] * n / rec["atoms"] if rec and rec.get("atoms") else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "k_force_mixed (fused VV)",
