@@ -9,14 +9,15 @@
 //
 // Mixed precision: pair arithmetic in FP32 on the cell-local shadow
 // coordinates (x_j - x_i = (s_j + delta h) - s_i, delta from the list entry's
-// stencil code); each lane keeps Kahan-compensated FP32 sums of its share of
-// the neighbors; the T lanes of an atom merge their (sum, compensation) pairs
-// with TwoSum in a fixed xor-shuffle tree; the result is converted to FP64
+// stencil code); each lane keeps a Kahan-compensated FP32 sum of its share of
+// the neighbors, adding one FMA-chained group of MD_FORCE_GROUP terms per
+// Kahan step; the T lanes of an atom fold their compensations and add their
+// partials in a fixed xor-shuffle order; the result is converted to FP64
 // once.  Velocities, positions and energy totals are FP64.
 //
-// Launch: persistent grid (SM count x resident CTAs); warp w of the grid takes
-// warp-tiles w, w + nwarps, ...; a warp-tile is A = 32/T consecutive atoms,
-// T lanes each.  The list row for step q of a warp-tile is one 128-byte load.
+// Launch: persistent grids (SM count x resident CTAs); a warp-tile is A = 32/T
+// consecutive atoms, T lanes each, and row q of its list block holds entry q
+// of each lane (one 128-byte row).
 //
 // Modes: FORCE_ONLY (store F, energy), FINAL (store F, v += dt/2 F/m, thermo),
 // FUSED (v += dt/2 F/m [thermo at v_n] v += dt/2 F/m, x += dt v, write the next
