@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -134,6 +135,66 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+# FP64 operations per list entry in the adjoint pair term (k_adjoint): within rc
+# (distance, one reciprocal, phi, psi, the Jacobian-vector product, the forces
+# and the two parameter partials) and beyond rc (distance and test only).
+ADJ_FLOPS_IN, ADJ_FLOPS_OUT = 86, 11
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def adjoint_leg(args, stream, dev):
+    """md_force_backward on the two-type 32,000-atom force-matching workload:
+    forward (md_compute_forces, FP64) and backward (the whole call: re-sort,
+    list rebuild, adjoint kernel, reductions) timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    import md_inputs as mi
+    from paper_2109_09056_b300 import MDSystem
+    from paper_2109_09056_b300 import api as A
+    sa = mi.workload("lj_2type_fcc20_32000")
+    m = MDSystem(sa.x, sa.v, sa.types, sa.box, ntypes=sa.ntypes, eps=sa.eps, sigma=sa.sigma,
+                 mass=sa.mass, rc=sa.rc, skin=sa.skin, dt=sa.dt, rebuild_every=sa.rebuild_every,
+                 precision="fp64", stream=stream)
+    G = torch.randn((sa.n, 3), dtype=torch.float64,
+                    generator=torch.Generator().manual_seed(5)).to(dev)
+    reps = max(args.steps, 5)
+    for _ in range(3):
+        m.compute_forces()
+        A.md_force_backward(m.ctx, G, 0.5)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        m.compute_forces()
+    ev[1].record(stream)
+    for _ in range(reps):
+        A.md_force_backward(m.ctx, G, 0.5)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd = ev[0].elapsed_time(ev[1]) / reps
+    bwd = ev[1].elapsed_time(ev[2]) / reps
+    # list entries and those within rc, from the GPU's own list and positions
+    st = m.state(forces=False)
+    x_int = st["x"][st["ids"]]
+    nn, rows = m.neighbors()
+    ii = np.repeat(np.arange(sa.n), nn)
+    jj = np.concatenate([rows[k, : nn[k]] for k in range(sa.n)])
+    d = x_int[jj] - x_int[ii]
+    d -= sa.box * np.round(d / sa.box)
+    within = int(np.count_nonzero((d * d).sum(1) < sa.rc ** 2))
+    flops = within * ADJ_FLOPS_IN + (ii.size - within) * ADJ_FLOPS_OUT
+    m.close()
+    achieved = flops / (bwd * 1e-3) / 1e12
+    return {"workload": "lj_2type_fcc20_32000", "atoms": sa.n, "precision": "fp64",
+            "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "value": sa.n / (bwd * 1e-3), "unit": "atoms/s (one md_force_backward)",
+            "fp64_view": {"achieved_tflops": achieved, "peak_tflops": FP64_NOMINAL_TFLOPS,
+                          "peak_source": "nominal", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                          "flops_per_call": flops, "list_entries": int(ii.size),
+                          "entries_within_rc": within}}
 
 
 def kernel_sources_sha256(files) -> str:
@@ -359,6 +420,10 @@ def run_ours(args, dist):
                "d2h_bytes_per_step": int(xo.numel() * 8 + vo.numel() * 8 + 112),
                "ms_per_step": 1e3 * el / args.steps}
         se.close()
+
+    # ---- force-matching adjoint (FP64) ---------------------------------------
+    if not args.no_adjoint:
+        out["adjoint"] = adjoint_leg(args, stream, dev)
 
     # ---- CPU baseline (oracle) on rank 0 at N = 1 ---------------------------
     cpu = None

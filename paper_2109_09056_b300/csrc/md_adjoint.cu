@@ -117,11 +117,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjArgs a) {
             const double u = (dx * dx + dy * dy) + dz * dz;
             if (!(u < rc2)) continue;
             const int ab = ti * nt + a.type[j];
-            const double q2 = t_s2[ab] / u;
+            const double iu = 1.0 / u;
+            const double q2 = t_s2[ab] * iu;
             const double s6 = q2 * q2 * q2, s12 = s6 * s6;
-            const double e24u = t_e24[ab] / u;
+            const double e24u = t_e24[ab] * iu;
             const double phi = e24u * (2.0 * s12 - s6);
-            const double psi = 2.0 * (e24u / u) * (4.0 * s6 - 14.0 * s12);
+            const double psi = 2.0 * (e24u * iu) * (4.0 * s6 - 14.0 * s12);
             const double Gdx = gix - a.G[j], Gdy = giy - a.G[a.ns + j], Gdz = giz - a.G[2 * a.ns + j];
             const double dG = dx * Gdx + dy * Gdy + dz * Gdz;
             gx += phi * Gdx + psi * dx * dG;
