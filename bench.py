@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-drift", action="store_true")
     return ap.parse_args()
 
 
@@ -195,6 +196,33 @@ def adjoint_leg(args, stream, dev):
                           "peak_source": "nominal", "frac": achieved / FP64_NOMINAL_TFLOPS,
                           "flops_per_call": flops, "list_entries": int(ii.size),
                           "entries_within_rc": within}}
+
+
+def drift_leg(stream):
+    """Energy conservation on the 131,072-atom melt (32^3 FCC cells, T* 1.44):
+    1000 NVE steps, mixed and FP64, total energy logged every 50 steps."""
+    import numpy as np
+
+    import md_inputs as mi
+    from paper_2109_09056_b300 import MDSystem
+    s = mi.workload("lj_fcc32_131072")
+    res = {"workload": "lj_fcc32_131072", "atoms": s.n, "md_steps": 1000, "thermo_every": 50}
+    logs = {}
+    for prec in ("mixed", "fp64"):
+        m = MDSystem(s.x, s.v, s.types, s.box, precision=prec, rc=s.rc, skin=s.skin, dt=s.dt,
+                     rebuild_every=s.rebuild_every, thermo_every=50, stream=stream)
+        m.step(1000)
+        lg = m.thermo_log()
+        m.close()
+        e = lg[:, 3] / s.n                            # total energy per atom
+        slope = float(np.polyfit(lg[:, 0], e, 1)[0])
+        logs[prec] = e
+        res[prec] = {"etot_per_atom_start": float(e[0]), "etot_per_atom_end": float(e[-1]),
+                     "drift_per_atom": float(e[-1] - e[0]),
+                     "slope_per_atom_per_1000_steps": slope * 1000.0,
+                     "max_abs_dev_per_atom": float(np.abs(e - e[0]).max())}
+    res["max_abs_etot_mixed_minus_fp64_per_atom"] = float(np.abs(logs["mixed"] - logs["fp64"]).max())
+    return res
 
 
 def kernel_sources_sha256(files) -> str:
@@ -420,6 +448,10 @@ def run_ours(args, dist):
                "d2h_bytes_per_step": int(xo.numel() * 8 + vo.numel() * 8 + 112),
                "ms_per_step": 1e3 * el / args.steps}
         se.close()
+
+    # ---- energy drift, mixed vs FP64 ------------------------------------------
+    if not args.no_drift:
+        out["energy_drift"] = drift_leg(stream)
 
     # ---- force-matching adjoint (FP64) ---------------------------------------
     if not args.no_adjoint:
