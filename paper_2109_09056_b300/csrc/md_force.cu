@@ -387,6 +387,9 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     const float c1x2_0 = 2.0f * c1_0;
     const size_t rowblk = (size_t)a.R * 32;  // words in one warp-tile's list block
     const uint64_t pol = l2_evict_first_policy();
+    // the same storage as three 32-float arrays per warp (x, y, z offsets)
+    float(*s_offs)[4][32] = reinterpret_cast<float(*)[4][32]>(s_off);
+    (void)s_offs;
     const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(lbuf + (size_t)wib * 2 * rowblk);
     const uint32_t bstride = (uint32_t)(rowblk * 4);  // bytes per buffer half
 #if MD_FORCE_LIST
@@ -437,13 +440,18 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         const int b = a.tile_box[(wt * A) >> 5];
         const Box &B = a.boxes[b];
         if (b != curbox) {
-            if (lane >= 27) {
-                s_off[wib][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
+            float4 ol = make_float4(0.f, 0.f, 0.f, 0.f);  // codes 27..31 unused
+            if (lane < 27) {
                 const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-                s_off[wib][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
-                                               (float)oz * B.hf[2], 0.f);
+                ol = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1], (float)oz * B.hf[2], 0.f);
             }
+#if MD_FORCE_OFFSET_SOA
+            s_offs[wib][0][lane] = ol.x;
+            s_offs[wib][1][lane] = ol.y;
+            s_offs[wib][2][lane] = ol.z;
+#else
+            s_off[wib][lane] = ol;
+#endif
             curbox = b;
         }
         const bool valid = (i - B.slot_off) < B.n;
@@ -470,7 +478,12 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
         auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
                          float &tp) {
+#if MD_FORCE_OFFSET_SOA
+            const unsigned cd = en >> MD_IDX_BITS;
+            const float4 o = make_float4(s_offs[wib][0][cd], s_offs[wib][1][cd], s_offs[wib][2][cd], 0.f);
+#else
             const float4 o = s_off[wib][en >> MD_IDX_BITS];
+#endif
             const float dx = (sj.x + o.x) - si.x;
             const float dy = (sj.y + o.y) - si.y;
             const float dz = (sj.z + o.z) - si.z;
