@@ -23,12 +23,15 @@
 // FUSED (v += dt/2 F/m [thermo at v_n] v += dt/2 F/m, x += dt v, write the next
 // shadow; the list-side reads use the current buffers, writes go to the
 // other buffer, so the kernel never reads what it writes).
+#include <algorithm>
+
 #include "md_common.cuh"
 
 namespace mdb {
 namespace {
 
-constexpr int kMaxWarps = 16;
+constexpr int kMaxWarps = 16;       // FP64 kernel: CTAs up to 256 threads
+constexpr int kMaxWarpsMixed = 24;  // mixed kernel: CTAs up to 768 threads
 constexpr int kBatch = MD_FORCE_BATCH;        // list entries per lane per batch
 constexpr uint32_t kNoEntry = 0xFFFFFFFFu;   // code 31: zero offset, far position
 
@@ -601,18 +604,22 @@ __device__ __forceinline__ void kernel_done(const ForceArgs &a, int64_t clock, b
     }
 }
 
+// Register budget: the share of MD_FORCE_MINB resident 128-thread CTAs per SM,
+// rounded down to the allocation granule of 8 (80 at 6); CTAs of 64 to 768
+// threads (kMaxWarpsMixed warps) fit it.
+#define MD_FORCE_MAXREG (65536 / (MD_FORCE_MINB * 128) / 8 * 8)
+static_assert(MD_FORCE_MAXREG * kMaxWarpsMixed * 32 <= 65536, "a full-size CTA must fit the SM");
+
 template <int T, bool ONE>
-// Register budget: MD_FORCE_MINB resident 128-thread CTAs per SM (the same
-// per-thread budget serves 64- and 256-thread CTAs).
-__global__ void __launch_bounds__(256, (MD_FORCE_MINB + 1) / 2) k_force_mixed(ForceArgs a) {
+__global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
         mirror_state(a);
         return;
     }
     extern __shared__ __align__(128) uint32_t lbuf[];
     __shared__ SmemTabs tb;
-    __shared__ __align__(16) float4 s_off[8][32];
-    __shared__ __align__(8) uint64_t s_bar[8][2];
+    __shared__ __align__(16) float4 s_off[kMaxWarpsMixed][32];
+    __shared__ __align__(8) uint64_t s_bar[kMaxWarpsMixed][2];
     load_tabs(*a.pair, tb);
     __syncthreads();
     const int64_t clock = a.fl->clock;
@@ -808,21 +815,22 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
     } else {
-        static int grid_cache[9][2][9] = {};
-        int &g = grid_cache[T][ONE][(c->block / 32) & 7];
+        const int block = std::min(c->block, kMaxWarps * 32);
+        static int grid_cache[9][2][kMaxWarps + 1] = {};
+        int &g = grid_cache[T][ONE][block / 32];
         if (g == 0) {
             int per = 0;
             cudaError_t e =
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force64<T, ONE>, c->block, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force64<T, ONE>, block, 0);
             if (e != cudaSuccess) return e;
             g = per > 0 ? per : 1;
         }
-        const int64_t warps_per_block = c->block / 32;
+        const int64_t warps_per_block = block / 32;
         int64_t grid = (int64_t)c->nsm * g;
         const int64_t need = (a.nwt + warps_per_block - 1) / warps_per_block;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
-        k_force64<T, ONE><<<(unsigned)grid, c->block, 0, c->stream>>>(a);
+        k_force64<T, ONE><<<(unsigned)grid, block, 0, c->stream>>>(a);
     }
     c->kernels += 1;
     return cudaGetLastError();
