@@ -273,9 +273,9 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     c->T = p.lanes_per_atom ? p.lanes_per_atom : 4;
     if (c->T != 1 && c->T != 2 && c->T != 4 && c->T != 8)
         return fail(c, MD_ERR_ARG, "lanes_per_atom must be 1, 2, 4 or 8");
-    c->block = p.block_threads ? p.block_threads : 256;
-    if (c->block < 64 || c->block > 768 || c->block % 32)
-        return fail(c, MD_ERR_ARG, "block_threads must be 64..768, a multiple of 32");
+    c->block = p.block_threads;  // 0: chosen per launch (md_force.cu)
+    if (c->block != 0 && (c->block < 64 || c->block > 768 || c->block % 32))
+        return fail(c, MD_ERR_ARG, "block_threads must be 0 or 64..768, a multiple of 32");
     md_status s = setup_pair(c, p.eps, p.sigma);
     if (s) return s;
     c->stream = static_cast<cudaStream_t>(stream);

@@ -47,7 +47,7 @@
 // Stencil-offset table of the mixed kernel: 0 = 27 float4 entries (one 16-byte
 // shared load per list entry), 1 = three 32-float arrays (three 4-byte loads).
 #ifndef MD_FORCE_OFFSET_SOA
-#define MD_FORCE_OFFSET_SOA 0
+#define MD_FORCE_OFFSET_SOA 1
 #endif
 // List terms combined by an FMA chain before each Kahan add (divides MD_FORCE_BATCH).
 #ifndef MD_FORCE_GROUP

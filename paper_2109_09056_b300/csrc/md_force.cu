@@ -785,13 +785,30 @@ __global__ void k_get_neighbors(const Box *__restrict__ boxes, const int32_t *__
     }
 }
 
+// Mixed-kernel CTA size when md_params.block_threads is 0.  Every size below
+// keeps 24 warps per SM under the register cap (1 x 768, 2 x 384, 3 x 256,
+// 6 x 128 threads); the largest is best on B300 (one CTA per SM walks one
+// contiguous run of warp-tiles, so all 24 warps share neighbors in L1: 0.79 ms
+// vs 0.81-0.83 ms at 256 for the 4M-atom melt), but a CTA must leave every SM
+// some tiles and its list buffers must fit in shared memory.
+int auto_block_mixed(const md_ctx *c, int64_t nwt, size_t per_warp_smem) {
+    constexpr size_t kSmemDyn = 200 * 1024;  // dynamic shared memory a CTA may take
+    static const int sizes[] = {768, 384, 256, 128, 64};
+    for (int b : sizes) {
+        const int w = b / 32;
+        if ((size_t)w * per_warp_smem <= kSmemDyn && nwt >= (int64_t)w * c->nsm) return b;
+    }
+    return 64;
+}
+
 template <bool MIXED, int T, bool ONE>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if constexpr (MIXED) {
-        // 2, 4 or 8 warps per CTA, each with a double buffer of R list rows.
-        const int block = c->block;
+        // Each warp has a double buffer of R list rows in shared memory.
+        const size_t per_warp = (size_t)2 * a.R * 32 * sizeof(uint32_t);
+        const int block = c->block ? c->block : auto_block_mixed(c, a.nwt, per_warp);
         const int warps = block / 32;
-        const size_t smem = (size_t)warps * 2 * a.R * 32 * sizeof(uint32_t);
+        const size_t smem = (size_t)warps * per_warp;
         static size_t smem_set = 0, occ_smem = 0;
         static int occ = 0, occ_block = 0;
         if (smem > smem_set) {
@@ -815,7 +832,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
     } else {
-        const int block = std::min(c->block, kMaxWarps * 32);
+        const int block = c->block ? std::min(c->block, kMaxWarps * 32) : kMaxWarps * 32;
         static int grid_cache[9][2][kMaxWarps + 1] = {};
         int &g = grid_cache[T][ONE][block / 32];
         if (g == 0) {

@@ -25,7 +25,7 @@ import time
 from typing import Callable, Iterable
 
 LANES = (1, 2, 4, 8)
-BLOCKS = (64, 128, 256)
+BLOCKS = (128, 256, 768)
 PAD_SLACK = (8, 16, 32)
 CADENCES = (5, 10, 15, 20, 25)
 
