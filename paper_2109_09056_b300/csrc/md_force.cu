@@ -30,7 +30,8 @@
 namespace mdb {
 namespace {
 
-constexpr int kMaxWarps = 16;       // FP64 kernel: CTAs up to 256 threads
+constexpr int kBlock64 = 256;       // FP64 kernel: CTAs of up to 256 threads
+constexpr int kMaxWarps = kBlock64 / 32;
 constexpr int kMaxWarpsMixed = 24;  // mixed kernel: CTAs up to 768 threads
 constexpr int kBatch = MD_FORCE_BATCH;        // list entries per lane per batch
 constexpr uint32_t kNoEntry = 0xFFFFFFFFu;   // code 31: zero offset, far position
@@ -630,7 +631,7 @@ __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
 }
 
 template <int T, bool ONE>
-__global__ void __launch_bounds__(256, 2) k_force64(ForceArgs a) {
+__global__ void __launch_bounds__(kBlock64, 2) k_force64(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
         mirror_state(a);
         return;
@@ -832,7 +833,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
     } else {
-        const int block = c->block ? std::min(c->block, kMaxWarps * 32) : kMaxWarps * 32;
+        const int block = c->block ? std::min(c->block, kBlock64) : kBlock64;
         static int grid_cache[9][2][kMaxWarps + 1] = {};
         int &g = grid_cache[T][ONE][block / 32];
         if (g == 0) {

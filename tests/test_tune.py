@@ -13,7 +13,7 @@ def fake_timer(factory, params, periods, steps, n):
     # longer cadence faster, but cadences above 15 are "dangerous"
     rate = 1e9
     rate *= {1: 0.5, 2: 0.8, 4: 1.0, 8: 0.7}[params["lanes_per_atom"]]
-    rate *= {64: 0.9, 128: 1.0, 256: 0.95}[params["block_threads"]]
+    rate *= {64: 0.9, 128: 1.0, 256: 0.95, 384: 0.93, 768: 0.9}[params["block_threads"]]
     if "neigh_pad" in params:
         rate *= 1.05 if params["neigh_pad"] == 90 + 16 else 1.01
     rate *= 1.0 + 0.01 * params["rebuild_every"]
