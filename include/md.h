@@ -75,9 +75,10 @@ typedef struct {
     int32_t thermo_every;        /* >0: log PE/KE/T/momentum every k steps (md_get_thermo_log) */
     int32_t neigh_pad;           /* list slots per atom; 0 = automatic (grown on overflow) */
     int32_t lanes_per_atom;      /* 1, 2, 4 or 8 lanes per atom in the force kernel; 0 = auto */
-    int32_t block_threads;       /* mixed force-kernel CTA size (64..768, multiple of 32; the
-                                    FP64 kernel uses at most 256); 0 = automatic (768 when the
-                                    system has enough warp-tiles and the list buffers fit) */
+    int32_t block_threads;       /* mixed force-kernel CTA size (64..768, multiple of 32; an
+                                    upper bound when its list buffers would not fit in shared
+                                    memory; the FP64 kernel uses at most 256); 0 = automatic
+                                    (768 when the system has enough warp-tiles and it fits) */
     int32_t use_graphs;          /* 1: md_step replays one rebuild period as a CUDA graph */
 } md_params;
 

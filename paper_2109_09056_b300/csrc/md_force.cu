@@ -792,8 +792,9 @@ __global__ void k_get_neighbors(const Box *__restrict__ boxes, const int32_t *__
 // contiguous run of warp-tiles, so all 24 warps share neighbors in L1: 0.79 ms
 // vs 0.81-0.83 ms at 256 for the 4M-atom melt), but a CTA must leave every SM
 // some tiles and its list buffers must fit in shared memory.
+constexpr size_t kSmemDyn = 200 * 1024;  // dynamic shared memory a mixed-kernel CTA may take
+
 int auto_block_mixed(const md_ctx *c, int64_t nwt, size_t per_warp_smem) {
-    constexpr size_t kSmemDyn = 200 * 1024;  // dynamic shared memory a CTA may take
     static const int sizes[] = {768, 384, 256, 128, 64};
     for (int b : sizes) {
         const int w = b / 32;
@@ -807,7 +808,10 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if constexpr (MIXED) {
         // Each warp has a double buffer of R list rows in shared memory.
         const size_t per_warp = (size_t)2 * a.R * 32 * sizeof(uint32_t);
-        const int block = c->block ? c->block : auto_block_mixed(c, a.nwt, per_warp);
+        int block = c->block ? c->block : auto_block_mixed(c, a.nwt, per_warp);
+        // an explicit size is an upper bound: fewer warps when their buffers
+        // would not fit in shared memory
+        while (block > 32 && (size_t)(block / 32) * per_warp > kSmemDyn) block -= 32;
         const int warps = block / 32;
         const size_t smem = (size_t)warps * per_warp;
         static size_t smem_set = 0, occ_smem = 0;

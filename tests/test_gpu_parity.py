@@ -67,6 +67,22 @@ def test_lanes_per_atom_variants(precision, lanes):
     assert gpu_sets_by_original_id(sysm) == oracle_sets_by_original_id(s.x, s.box)
 
 
+@pytest.mark.parametrize("lanes,block", [(1, 768), (2, 768), (4, 384), (8, 64)])
+def test_cta_sizes_and_wide_rows(lanes, block):
+    """Explicit CTA sizes, including ones whose per-warp list buffers do not all
+    fit in shared memory at 768 threads (the kernel then runs fewer warps per
+    CTA): same forces as the oracle and the same trajectory as the default."""
+    s = mi.lj_melt(12, seed=13, jitter=0.1)         # 6912 atoms
+    a = make(s, "mixed", lanes_per_atom=lanes, block_threads=block)
+    f_o, _, _ = oracle.lj_forces(oracle.wrap(s.x, s.box)[0], s.types, s.box)
+    a.compute_forces()
+    assert rel_l2(a.state()["f"], f_o) <= 1e-5
+    b = make(s, "mixed", lanes_per_atom=lanes)
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.state()["x"], b.state()["x"])   # the CTA size changes no arithmetic
+
+
 def test_two_types_forces_both_precisions():
     s = mi.two_type_melt(8, seed=8)
     f_o, _, pe_o = oracle.lj_forces(oracle.wrap(s.x, s.box)[0], s.types, s.box, eps=s.eps,
