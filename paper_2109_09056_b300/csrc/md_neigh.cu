@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
     __shared__ int64_t s_start[kWarps][27];
     __shared__ int32_t s_pref[kWarps][28];
     __shared__ __align__(16) float4 hpos[kWarps][32];
-    __shared__ __align__(16) uint4 masks[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * kWarps + w;
     if (c >= a.ncell) return;  // whole warp
@@ -192,10 +191,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
             __syncwarp();
             for (int g0 = 0; g0 < Mp; g0 += 64) {
                 // Test phase: lane = candidates g0 + lane and g0 + 32 + lane
-                // against every home atom; home atom hh's four ballots go to
-                // masks[w][hh] (one lane's 16-byte store), read back by lane hh.
+                // against every home atom; home atom hh's ballots land in lane hh.
                 const float4 c0 = cand[w][g0 + lane], c1 = cand[w][g0 + 32 + lane];
-                __syncwarp();  // the previous chunk pair's masks have been read
+                unsigned hi0 = 0u, lo0 = 0u, hi1 = 0u, lo1 = 0u;
                 for (int hh = 0; hh < nh; ++hh) {
                     const float4 h = hpos[w][hh];
                     const float dx0 = c0.x - h.x, dy0 = c0.y - h.y, dz0 = c0.z - h.z;
@@ -206,13 +204,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_build(BuildArgs a) {
                     const unsigned bl0 = __ballot_sync(0xffffffffu, r20 < lo);
                     const unsigned bh1 = __ballot_sync(0xffffffffu, r21 <= hi);
                     const unsigned bl1 = __ballot_sync(0xffffffffu, r21 < lo);
-                    if (lane == 0) masks[w][hh] = make_uint4(bh0, bl0, bh1, bl1);
+                    if (lane == hh) {
+                        hi0 = bh0; lo0 = bl0; hi1 = bh1; lo1 = bl1;
+                    }
                 }
-                __syncwarp();
                 if (!active) continue;
-                const uint4 m = masks[w][lane];
-                write_chunk(g0, m.x, m.y);
-                write_chunk(g0 + 32, m.z, m.w);
+                write_chunk(g0, hi0, lo0);
+                write_chunk(g0 + 32, hi1, lo1);
             }
         }
         if (active) {
