@@ -409,7 +409,10 @@ const void *dev_input(md_ctx *c, const void *p, size_t bytes, size_t stage_off, 
     return s + stage_off;
 }
 
-md_status load_state(md_ctx *c, const double *x, const double *v, const int32_t *types) {
+// `types` from the caller are range-checked; the context's own (md_set_state
+// reloading the current types) are not.
+md_status load_state(md_ctx *c, const double *x, const double *v, const int32_t *types,
+                     bool check_types = true) {
     const size_t n = (size_t)c->n_total;
     md_status st;
     // stage layout: x | v | types (host inputs only); sized once so that no
@@ -422,7 +425,7 @@ md_status load_state(md_ctx *c, const double *x, const double *v, const int32_t 
     if (st) return st;
     const void *dt = dev_input(c, types, n * sizeof(int32_t), 6 * n * sizeof(double), &st);
     if (st) return st;
-    if (types) {
+    if (types && check_types) {
         std::vector<int32_t> h(n);
         if (is_device_ptr(types)) {
             CK(cudaMemcpy(h.data(), types, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -891,7 +894,7 @@ md_status md_set_state(md_ctx *c, const double *x, const double *v) {
     double *vcur = xcur + 3 * n;
     int32_t *tcur = reinterpret_cast<int32_t *>(vcur + 3 * n);
     CK(launch_get_state(c, x ? nullptr : xcur, v ? nullptr : vcur, nullptr, nullptr, nullptr, tcur));
-    md_status s = load_state(c, x ? x : xcur, v ? v : vcur, tcur);
+    md_status s = load_state(c, x ? x : xcur, v ? v : vcur, tcur, false);
     if (s) return s;
     invalidate_graphs(c);
     s = sort_build_forces(c, true);
