@@ -138,6 +138,15 @@ def peaks():
         return {}
 
 
+# Algorithmic bytes per atom of one re-sort (non-raw): k_bin reads r, the packed
+# cell and r_build, writes the wrapped x, cell and rank (84 B); k_scatter 16 B;
+# the per-cell ordering 8 B; k_permute gathers perm, cell, x, v, type, id, images
+# (76 B) and writes r, r_build, x, v, type, id, images, cell, shadow, count (140 B).
+SORT_BYTES_PER_ATOM = 84.0 + 16.0 + 8.0 + 76.0 + 140.0
+# The list build writes every slot of its rows (4 B x pad) and reads each atom's
+# shadow once from DRAM plus its count and cell bookkeeping.
+BUILD_BYTES_PER_ATOM = 16.0 + 4.0
+
 # FP64 operations per list entry in the adjoint pair term (k_adjoint): within rc
 # (distance, one reciprocal, phi, psi, the Jacobian-vector product, the forces
 # and the two parameter partials) and beyond rc (distance and test only).
@@ -327,6 +336,7 @@ def run_ours(args, dist):
     ms = e0.elapsed_time(e1)
     launches = sysm.launch_count() - k0
     n_force, force_ms, alg_bytes = sysm.profile_read()
+    n_reb, sort_ms, build_ms = sysm.profile_rebuild()
     sysm.profile(False)
     ms_max = dist.max(ms)
     value = n * MD_PER_STEP * args.steps * dist.world / (ms_max * 1e-3)
@@ -421,6 +431,23 @@ def run_ours(args, dist):
                             "peak_tops": issue / 1e12, "frac": n * ops_atom / t_launch / issue,
                             "sm_mhz": sm_mhz, "ops_per_atom": ops_atom}
 
+    # ---- the rebuild kernels of the timed region (re-sort, list build) ------
+    rebuild = None
+    if n_reb > 0:
+        t_sort = sort_ms / n_reb * 1e-3
+        t_build = build_ms / n_reb * 1e-3
+        pad = sysm.thermo()["pad"]
+        sort_bytes = n * SORT_BYTES_PER_ATOM
+        build_bytes = n * (4.0 * pad + BUILD_BYTES_PER_ATOM)
+        hbm = pk.get("hbm_gbs")
+        rebuild = {"rebuilds": n_reb,
+                   "sort_ms": t_sort * 1e3, "build_ms": t_build * 1e3,
+                   "sort_hbm_view": {"bytes": sort_bytes, "achieved_gbs": sort_bytes / t_sort / 1e9,
+                                     "peak_gbs": hbm, "frac": sort_bytes / t_sort / 1e9 / hbm if hbm else None},
+                   "build_hbm_view": {"bytes": build_bytes, "achieved_gbs": build_bytes / t_build / 1e9,
+                                      "peak_gbs": hbm, "frac": build_bytes / t_build / 1e9 / hbm if hbm else None,
+                                      "note": "the build is issue-bound (candidate tests), not DRAM-bound"}}
+
     # ---- end to end through the C ABI with pinned host buffers ------------
     e2e = None
     if not args.no_e2e:
@@ -479,6 +506,8 @@ def run_ours(args, dist):
             "clocks": clocks,
             "final_thermo": {"pe_per_atom": th["pe"] / n, "temperature": th["temperature"],
                              "dangerous_builds": th["dangerous_builds"], "nn_max": th["nn_max"]}}
+    if rebuild is not None:
+        line["rebuild"] = rebuild
     line.update(out)
     sysm.close()
     if dist.rank == 0:

@@ -208,6 +208,10 @@ md_status md_get_thermo_log(md_ctx *ctx, double *rows, int32_t *count);
  * algorithmic count (list entries + positions + state), and resets. */
 md_status md_profile(md_ctx *ctx, int32_t on);
 md_status md_profile_read(md_ctx *ctx, int64_t *launches, double *ms, double *alg_bytes);
+/* The same for the rebuilds md_step performs while profiling is on: their
+ * number and the summed device time (ms) of the re-sort (binning, scan,
+ * permutation, state gather) and of the list build since the last call. */
+md_status md_profile_rebuild(md_ctx *ctx, int64_t *rebuilds, double *sort_ms, double *build_ms);
 
 /* Number of library kernels enqueued on this context since creation (graph
  * replays count every kernel node of the replayed graph). */

@@ -10,7 +10,7 @@ is ``md_force_backward``.  PyTorch provides device memory and streams.
 from .api import (MDSystem, md_batch_create, md_bin_sort_noalloc, md_batch_thermo, md_bin_sort, md_build_neighbors,
                   md_compute_forces, md_create, md_destroy, md_force_backward, md_get_neighbors,
                   md_get_permutation, md_get_state, md_get_thermo, md_get_thermo_log, md_info,
-                  md_debug_expire_waits, md_launch_count, md_params_default, md_profile, md_profile_read, md_set_params,
+                  md_debug_expire_waits, md_launch_count, md_params_default, md_profile, md_profile_read, md_profile_rebuild, md_set_params,
                   md_set_positions, md_set_state, md_step)
 from ._native import LIB_PATH, MD_FP64, MD_MIXED, MDError
 
@@ -18,7 +18,7 @@ __all__ = [
     "MDSystem", "MDError", "LIB_PATH", "MD_FP64", "MD_MIXED", "md_create", "md_bin_sort",
     "md_build_neighbors", "md_compute_forces", "md_step", "md_force_backward", "md_set_positions",
     "md_set_state", "md_launch_count", "md_debug_expire_waits", "md_bin_sort_noalloc", "md_set_params", "md_get_state", "md_get_permutation", "md_get_neighbors", "md_get_thermo",
-    "md_get_thermo_log", "md_profile", "md_profile_read", "md_destroy", "md_batch_create",
+    "md_get_thermo_log", "md_profile", "md_profile_read", "md_profile_rebuild", "md_destroy", "md_batch_create",
     "md_batch_thermo", "md_info", "md_params_default", "LJForce",
 ]
 

@@ -80,6 +80,8 @@ SIGNATURES = {
     "md_profile": ([P, C.c_int32], C.c_int),
     "md_profile_read": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "md_launch_count": ([P, C.POINTER(C.c_int64)], C.c_int),
+    "md_profile_rebuild": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)],
+                           C.c_int),
     "md_debug_expire_waits": ([P, C.c_int32], C.c_int),
     "md_last_error": ([P], C.c_char_p),
     "md_destroy": ([P], None),

@@ -255,6 +255,15 @@ def md_profile_read(ctx: Ctx) -> tuple:
     return k.value, ms.value, by.value
 
 
+def md_profile_rebuild(ctx: Ctx) -> tuple:
+    """(rebuilds, summed re-sort ms, summed list-build ms) since the last call."""
+    k = C.c_int64()
+    ms_s = C.c_double()
+    ms_b = C.c_double()
+    check(lib.md_profile_rebuild(ctx.handle, C.byref(k), C.byref(ms_s), C.byref(ms_b)), ctx.handle)
+    return k.value, ms_s.value, ms_b.value
+
+
 def md_launch_count(ctx: Ctx) -> int:
     k = C.c_int64()
     check(lib.md_launch_count(ctx.handle, C.byref(k)), ctx.handle)
@@ -334,6 +343,9 @@ class MDSystem:
 
     def launch_count(self) -> int:
         return md_launch_count(self.ctx)
+
+    def profile_rebuild(self) -> tuple:
+        return md_profile_rebuild(self.ctx)
 
     def set_params(self, eps=None, sigma=None):
         md_set_params(self.ctx, eps, sigma)

@@ -464,6 +464,35 @@ md_status mdb::set_global_error(md_status s, const std::string &msg) {
     return s;
 }
 
+// With profiling on, `launch` is bracketed by a pair of CUDA events tagged
+// 0 (force), 1 (re-sort) or 2 (list build).
+template <typename F>
+static md_status record_timed(md_ctx *c, int tag, F &&launch) {
+    if (!c->prof) {
+        CK(launch());
+        return MD_OK;
+    }
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->ev_pool.push_back(e);
+        }
+    }
+    cudaEvent_t e0 = c->ev_pool[c->ev_used], e1 = c->ev_pool[c->ev_used + 1];
+    c->ev_tag.resize(c->ev_used / 2 + 1);
+    c->ev_tag[c->ev_used / 2] = tag;
+    c->ev_used += 2;
+    CK(cudaEventRecord(e0, c->stream));
+    CK(launch());
+    CK(cudaEventRecord(e1, c->stream));
+    return MD_OK;
+}
+
+static md_status record_force(md_ctx *c, int mode) {
+    return record_timed(c, 0, [&] { return launch_force(c, mode); });
+}
+
 extern "C" {
 
 void md_params_default(md_params *p) {
@@ -568,34 +597,17 @@ md_status md_compute_forces(md_ctx *c, double *energy_out) {
     return MD_OK;
 }
 
-static md_status record_force(md_ctx *c, int mode) {
-    if (!c->prof) {
-        CK(launch_force(c, mode));
-        return MD_OK;
-    }
-    if (c->ev_used + 2 > c->ev_pool.size()) {
-        for (int k = 0; k < 64; ++k) {
-            cudaEvent_t e;
-            CK(cudaEventCreate(&e));
-            c->ev_pool.push_back(e);
-        }
-    }
-    cudaEvent_t e0 = c->ev_pool[c->ev_used], e1 = c->ev_pool[c->ev_used + 1];
-    c->ev_used += 2;
-    CK(cudaEventRecord(e0, c->stream));
-    CK(launch_force(c, mode));
-    CK(cudaEventRecord(e1, c->stream));
-    return MD_OK;
-}
-
 static md_status flush_profile_events(md_ctx *c) {
     if (c->ev_used == 0) return MD_OK;
     CK(cudaStreamSynchronize(c->stream));
     for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev_pool[k], c->ev_pool[k + 1]));
-        c->prof_ms += ms;
-        c->prof_launches += 1;
+        switch (c->ev_tag[k / 2]) {
+            case 0: c->prof_ms += ms; c->prof_launches += 1; break;
+            case 1: c->prof_sort_ms += ms; c->prof_rebuilds += 1; break;
+            default: c->prof_build_ms += ms; break;
+        }
     }
     c->ev_used = 0;
     return MD_OK;
@@ -676,8 +688,10 @@ md_status md_step(md_ctx *c, int32_t nsteps, md_thermo *last_out) {
                 continue;
             }
             if (n % every == 0 && c->built_at != n) {
-                CK(launch_bin_sort(c, false));
-                CK(launch_build(c));
+                s = record_timed(c, 1, [&] { return launch_bin_sort(c, false); });
+                if (s) return s;
+                s = record_timed(c, 2, [&] { return launch_build(c); });
+                if (s) return s;
                 c->sorted_at = n;
                 c->built_at = n;
                 c->list_valid = true;
@@ -927,7 +941,21 @@ md_status md_profile(md_ctx *c, int32_t on) {
     c->prof = on != 0;
     c->prof_launches = 0;
     c->prof_ms = 0.0;
+    c->prof_rebuilds = 0;
+    c->prof_sort_ms = c->prof_build_ms = 0.0;
     c->ev_used = 0;
+    return MD_OK;
+}
+
+md_status md_profile_rebuild(md_ctx *c, int64_t *rebuilds, double *sort_ms, double *build_ms) {
+    if (!c) return MD_ERR_ARG;
+    md_status s = flush_profile_events(c);
+    if (s) return s;
+    if (rebuilds) *rebuilds = c->prof_rebuilds;
+    if (sort_ms) *sort_ms = c->prof_sort_ms;
+    if (build_ms) *build_ms = c->prof_build_ms;
+    c->prof_rebuilds = 0;
+    c->prof_sort_ms = c->prof_build_ms = 0.0;
     return MD_OK;
 }
 

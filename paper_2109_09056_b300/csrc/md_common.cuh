@@ -198,8 +198,11 @@ struct md_ctx {
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_tag;       // per used event pair: 0 force, 1 re-sort, 2 list build
     size_t ev_used = 0;
     int64_t prof_launches = 0;
+    int64_t prof_rebuilds = 0;
+    double prof_sort_ms = 0.0, prof_build_ms = 0.0;
     int64_t kernels = 0;           // library kernels enqueued (see md_launch_count)
     uint32_t debug_tx_extra = 0;   // md_debug_expire_waits
     double prof_ms = 0.0;
