@@ -209,8 +209,10 @@ def adjoint_leg(args, stream, dev):
 
 def drift_leg(stream):
     """Energy conservation on the 131,072-atom melt (32^3 FCC cells, T* 1.44):
-    1000 NVE steps, mixed and FP64, total energy logged every 50 steps."""
+    1000 NVE steps, mixed and FP64, total energy logged every 50 steps (the
+    run's device time gives the throughput at this size too)."""
     import numpy as np
+    import torch
 
     import md_inputs as mi
     from paper_2109_09056_b300 import MDSystem
@@ -220,9 +222,15 @@ def drift_leg(stream):
     for prec in ("mixed", "fp64"):
         m = MDSystem(s.x, s.v, s.types, s.box, precision=prec, rc=s.rc, skin=s.skin, dt=s.dt,
                      rebuild_every=s.rebuild_every, thermo_every=50, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         m.step(1000)
+        e1.record(stream)
+        torch.cuda.synchronize()
         lg = m.thermo_log()
         m.close()
+        res.setdefault("atom_steps_per_s", {})[prec] = s.n * 1000 / (e0.elapsed_time(e1) * 1e-3)
         e = lg[:, 3] / s.n                            # total energy per atom
         slope = float(np.polyfit(lg[:, 0], e, 1)[0])
         logs[prec] = e
@@ -231,6 +239,32 @@ def drift_leg(stream):
                      "slope_per_atom_per_1000_steps": slope * 1000.0,
                      "max_abs_dev_per_atom": float(np.abs(e - e[0]).max())}
     res["max_abs_etot_mixed_minus_fp64_per_atom"] = float(np.abs(logs["mixed"] - logs["fp64"]).max())
+    return res
+
+
+def small_leg(stream):
+    """Throughput at the 4,000-atom size (10^3 FCC cells, 100 steps, rebuild
+    every 20), mixed and FP64: launch-bound, reported for completeness."""
+    import torch
+
+    import md_inputs as mi
+    from paper_2109_09056_b300 import MDSystem
+    s = mi.workload("lj_fcc10_4000")
+    res = {"workload": "lj_fcc10_4000", "atoms": s.n, "md_steps": 100}
+    for prec in ("mixed", "fp64"):
+        m = MDSystem(s.x, s.v, s.types, s.box, precision=prec, rc=s.rc, skin=s.skin, dt=s.dt,
+                     rebuild_every=s.rebuild_every, stream=stream)
+        m.step(100)                                   # warm-up (graphs captured)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.step(100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        m.close()
+        res[prec] = s.n * 100 / (e0.elapsed_time(e1) * 1e-3)
+    res["unit"] = "atom-steps/s"
     return res
 
 
@@ -479,6 +513,10 @@ def run_ours(args, dist):
     # ---- energy drift, mixed vs FP64 ------------------------------------------
     if not args.no_drift:
         out["energy_drift"] = drift_leg(stream)
+
+    # ---- the 4,000-atom configuration -----------------------------------------
+    if not args.no_drift:
+        out["small"] = small_leg(stream)
 
     # ---- force-matching adjoint (FP64) ---------------------------------------
     if not args.no_adjoint:
