@@ -74,14 +74,10 @@ __device__ __forceinline__ double sum_lanes_d(double x) {
     return x;
 }
 
-__device__ __forceinline__ double warp_sum_d(double x) {
+template <int T>
+__device__ __forceinline__ float sum_lanes_f(float x) {
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-__device__ __forceinline__ double warp_max_d(double x) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    for (int o = T / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
 
@@ -173,16 +169,29 @@ __device__ __forceinline__ void finish_tile(const ForceArgs &a, const SmemTabs &
         if (valid && sub == 0) a.sh_out[i] = make_float4(s3[0], s3[1], s3[2], __int_as_float(ti));
     }
     if (THERMO) {
-        // displacement^2 of the atom = sum over its components (spread over lanes)
-        const double dsum = sum_lanes_d<T>(disp2);
-        const double pe_t = warp_sum_d((valid && sub == 0) ? ped : 0.0);
-        const double ke_t = warp_sum_d(ke);
-        const double px = warp_sum_d(pd[0]), py = warp_sum_d(pd[1]), pz = warp_sum_d(pd[2]);
-        const double dm = warp_max_d(valid ? dsum : 0.0);
-        if (lane == 0) {
-            double *tp = a.tpart + wt * TP;
-            tp[0] = pe_t; tp[1] = ke_t; tp[2] = px; tp[3] = py; tp[4] = pz; tp[5] = dm;
+        // Five FP64 sums over the warp (PE, KE, Px, Py, Pz) by a butterfly
+        // that halves the values each lane carries per level (9 adds instead
+        // of 25); lane 4q ends with quantity q.  The largest displacement^2 of
+        // an atom (its components summed over its lanes) in FP32.
+        double q[8] = {(valid && sub == 0) ? ped : 0.0, ke, pd[0], pd[1], pd[2], 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
+            const bool up = lane & o;
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                const double give = up ? q[k] : q[k + h];
+                const double keep = up ? q[k + h] : q[k];
+                q[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+            }
         }
+        q[0] += __shfl_xor_sync(0xffffffffu, q[0], 2);
+        q[0] += __shfl_xor_sync(0xffffffffu, q[0], 1);
+        const float dsum = sum_lanes_f<T>((float)disp2);
+        const float dm = __uint_as_float(
+            __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(dsum) : 0u));
+        double *tp = a.tpart + wt * TP;
+        if ((lane & 3) == 0 && lane < 20) tp[lane >> 2] = q[0];
+        if (lane == 0) tp[5] = (double)dm;
     }
 }
 
@@ -364,13 +373,6 @@ __device__ __forceinline__ void cp_async_rows(uint32_t dst, const uint32_t *src,
 template <int T>
 __device__ __forceinline__ int tile_rows(int ni) {
     return __reduce_max_sync(0xffffffffu, (ni + T - 1) / T);
-}
-
-template <int T>
-__device__ __forceinline__ float sum_lanes_f(float x) {
-#pragma unroll
-    for (int o = T / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
 }
 
 template <int T, bool ONE, bool THERMO>
