@@ -39,16 +39,6 @@
 #ifndef MD_FORCE_MINB
 #define MD_FORCE_MINB 6   // measured best on B300 at 4M atoms (5: 1.03 ms, 6: 0.94 ms)
 #endif
-// List rows of a warp-tile into its shared-memory buffer: 1 = one bulk (TMA)
-// copy completing on an mbarrier; 0 = the warp's 16-byte cp.async copies.
-#ifndef MD_FORCE_LIST
-#define MD_FORCE_LIST 1
-#endif
-// Stencil-offset table of the mixed kernel: 0 = 27 float4 entries (one 16-byte
-// shared load per list entry), 1 = three 32-float arrays (three 4-byte loads).
-#ifndef MD_FORCE_OFFSET_SOA
-#define MD_FORCE_OFFSET_SOA 1
-#endif
 // List terms combined by an FMA chain before each Kahan add (divides MD_FORCE_BATCH).
 #ifndef MD_FORCE_GROUP
 #define MD_FORCE_GROUP 4

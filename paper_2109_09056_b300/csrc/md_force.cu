@@ -285,10 +285,12 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
 // Each warp walks a contiguous run of warp-tiles (the CTA's chunk, warps
 // interleaved, so the CTA's warps share neighbors in L1).  While it evaluates
 // tile t it has tile t + 1's list rows in flight into the other half of a
-// per-warp shared-memory double buffer: one bulk (TMA) copy per tile that
-// completes on an mbarrier (MD_FORCE_LIST 1), or 16-byte cp.async copies
-// (MD_FORCE_LIST 0); only as many 128-byte rows as the tile's longest row.
-// Neighbor shadows are gathered kBatch at a time per lane.
+// per-warp shared-memory double buffer: one bulk (TMA) copy per tile, only as
+// many 128-byte rows as the tile's longest row, completing on an mbarrier.
+// Neighbor shadows are gathered kBatch at a time per lane.  (Measured on B300
+// and dropped: 16-byte cp.async copies of the rows, 2% slower; a 27-entry
+// float4 offset table, read as one 16-byte load, 1-2% slower than three
+// 4-byte arrays.)
 
 // The list is read once per step: its copies carry an L2 evict-first policy so
 // they do not push out the neighbor shadows (small enough to stay in L2).
@@ -350,24 +352,6 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint64_t pol) {
-    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(saddr),
-                 "l"(g), "l"(pol)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// Rows [0, rows) of a list block -> shared dst with the whole warp's cp.async.
-__device__ __forceinline__ void cp_async_rows(uint32_t dst, const uint32_t *src, int rows, int lane,
-                                              uint64_t pol) {
-    for (int c = lane; c < rows * 8; c += 32) cp_async16(dst + 16u * c, src + 4 * c, pol);
-}
-
 // List rows a warp-tile needs: its longest row (rows past an atom's count hold
 // the sentinel entry).
 template <int T>
@@ -377,7 +361,7 @@ __device__ __forceinline__ int tile_rows(int ni) {
 
 template <int T, bool ONE, bool THERMO>
 __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
-                                           float4 (*s_off)[32], uint64_t (*s_bar)[2],
+                                           float (*s_off)[3][32], uint64_t (*s_bar)[2],
                                            uint32_t *lbuf) {
     constexpr int A = 32 / T;
     constexpr int G = MD_FORCE_GROUP;
@@ -393,12 +377,8 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     const float c1x2_0 = 2.0f * c1_0;
     const size_t rowblk = (size_t)a.R * 32;  // words in one warp-tile's list block
     const uint64_t pol = l2_evict_first_policy();
-    // the same storage as three 32-float arrays per warp (x, y, z offsets)
-    float(*s_offs)[4][32] = reinterpret_cast<float(*)[4][32]>(s_off);
-    (void)s_offs;
     const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(lbuf + (size_t)wib * 2 * rowblk);
     const uint32_t bstride = (uint32_t)(rowblk * 4);  // bytes per buffer half
-#if MD_FORCE_LIST
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[wib][0]);
     uint32_t phase = 0;  // bit k: parity of buffer k's next completion
     if (lane == 0) {
@@ -407,22 +387,12 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         fence_mbar_init();
     }
     __syncwarp();
-#else
-    (void)s_bar;
-#endif
     int64_t wt = t0 + wib;
     int rows_cur = 0;
     if (wt < t1) {
         rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
-#if MD_FORCE_LIST
         if (lane == 0) bulk_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, bar0, pol, a.tx_extra);
-#else
-        cp_async_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, lane, pol);
-#endif
     }
-#if !MD_FORCE_LIST
-    cp_async_commit();
-#endif
     int cb = 0;
     int curbox = -1;
     for (; wt < t1; wt += nwc) {
@@ -431,39 +401,24 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         int rows_next = 0;
         if (has_next) {
             rows_next = tile_rows<T>(min(__ldg(a.nn + wn * A + lane / T), a.pad));
-#if MD_FORCE_LIST
             if (lane == 0)
                 bulk_rows(sbuf0 + (cb ^ 1) * bstride, a.nbr + wn * rowblk, rows_next,
                           bar0 + 8 * (cb ^ 1), pol, a.tx_extra);
-#else
-            cp_async_rows(sbuf0 + (cb ^ 1) * bstride, a.nbr + wn * rowblk, rows_next, lane, pol);
-#endif
         }
-#if !MD_FORCE_LIST
-        cp_async_commit();
-#endif
         const int64_t i = wt * A + lane / T;
         const int b = a.tile_box[(wt * A) >> 5];
         const Box &B = a.boxes[b];
         if (b != curbox) {
-            float4 ol = make_float4(0.f, 0.f, 0.f, 0.f);  // codes 27..31 unused
-            if (lane < 27) {
-                const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-                ol = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1], (float)oz * B.hf[2], 0.f);
-            }
-#if MD_FORCE_OFFSET_SOA
-            s_offs[wib][0][lane] = ol.x;
-            s_offs[wib][1][lane] = ol.y;
-            s_offs[wib][2][lane] = ol.z;
-#else
-            s_off[wib][lane] = ol;
-#endif
+            // offset of stencil code `lane` (codes 27..31 unused: zero)
+            const bool code = lane < 27;
+            s_off[wib][0][lane] = code ? (float)(lane % 3 - 1) * B.hf[0] : 0.f;
+            s_off[wib][1][lane] = code ? (float)((lane / 3) % 3 - 1) * B.hf[1] : 0.f;
+            s_off[wib][2][lane] = code ? (float)(lane / 9 - 1) * B.hf[2] : 0.f;
             curbox = b;
         }
         const bool valid = (i - B.slot_off) < B.n;
         const float4 si = a.sh_in[i];
         const int ti = ONE ? 0 : __float_as_int(si.w);
-#if MD_FORCE_LIST
         // the current tile's rows have landed; a wait that runs out abandons
         // the step with a timeout status (after waiting, again bounded, for
         // the copy in flight into the other half)
@@ -473,10 +428,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             return;
         }
         phase ^= 1u << cb;
-#else
-        cp_async_wait<1>();  // this lane's copies of the current tile have landed
-#endif
-        __syncwarp();  // ... and every other lane's; s_off is visible too
+        __syncwarp();  // s_off is visible to the whole warp
         const uint32_t *Lr = lbuf + (size_t)wib * 2 * rowblk + cb * rowblk + lane;
         float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
         // One list entry: x_j - x_i from the shadows and the stencil offset,
@@ -484,15 +436,10 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
         auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
                          float &tp) {
-#if MD_FORCE_OFFSET_SOA
             const unsigned cd = en >> MD_IDX_BITS;
-            const float4 o = make_float4(s_offs[wib][0][cd], s_offs[wib][1][cd], s_offs[wib][2][cd], 0.f);
-#else
-            const float4 o = s_off[wib][en >> MD_IDX_BITS];
-#endif
-            const float dx = (sj.x + o.x) - si.x;
-            const float dy = (sj.y + o.y) - si.y;
-            const float dz = (sj.z + o.z) - si.z;
+            const float dx = (sj.x + s_off[wib][0][cd]) - si.x;
+            const float dy = (sj.y + s_off[wib][1][cd]) - si.y;
+            const float dz = (sj.z + s_off[wib][2][cd]) - si.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const bool in = r2 < rc2f;
             const float r2inv = __fdividef(1.0f, r2);
@@ -567,9 +514,6 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         cb ^= 1;
         rows_cur = rows_next;
     }
-#if !MD_FORCE_LIST
-    cp_async_wait<0>();
-#endif
 }
 
 // Frozen (a list overflowed, a position went non-finite or a wait ran out
@@ -621,7 +565,7 @@ __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
     }
     extern __shared__ __align__(128) uint32_t lbuf[];
     __shared__ SmemTabs tb;
-    __shared__ __align__(16) float4 s_off[kMaxWarpsMixed][32];
+    __shared__ __align__(16) float s_off[kMaxWarpsMixed][3][32];
     __shared__ __align__(8) uint64_t s_bar[kMaxWarpsMixed][2];
     load_tabs(*a.pair, tb);
     __syncthreads();
