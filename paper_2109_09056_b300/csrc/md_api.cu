@@ -72,6 +72,9 @@ void free_all(md_ctx *c) {
     for (auto &g : c->gexec)
         if (g) cudaGraphExecDestroy(g);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->ev_main) cudaEventDestroy(c->ev_main);
+    if (c->ev_side) cudaEventDestroy(c->ev_side);
+    if (c->side) cudaStreamDestroy(c->side);
 }
 
 void* stage_buffer(md_ctx *c, size_t bytes) {
@@ -199,21 +202,30 @@ md_status build_with_retry(md_ctx *c) {
     return fail(c, MD_ERR_NEIGH_OVERFLOW, "neighbor list kept overflowing");
 }
 
-md_status sort_build_forces(md_ctx *c, bool raw) {
+md_status sort_build(md_ctx *c, bool raw) {
     CK(launch_bin_sort(c, raw));
     c->sorted_at = c->step;
     c->built_at = c->step;
-    md_status s = build_with_retry(c);
-    if (s) return s;
+    return build_with_retry(c);
+}
+
+// Forces (and thermo) of a freshly sorted and listed state.
+md_status forces_at_build(md_ctx *c) {
     CK(launch_force(c, MODE_FORCE_ONLY));
     CK(launch_finalize(c, MODE_FORCE_ONLY));
-    s = read_flags(c);
+    md_status s = read_flags(c);
     if (s) return s;
     if (c->hflags->status & ST_TIMEOUT) return timeout_fail(c);
     if (c->hflags->status & ST_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position");
     c->forces_valid = true;
     c->ready = true;
     return MD_OK;
+}
+
+md_status sort_build_forces(md_ctx *c, bool raw) {
+    md_status s = sort_build(c, raw);
+    if (s) return s;
+    return forces_at_build(c);
 }
 
 void fill_thermo(md_ctx *c, int b, md_thermo *t) {
@@ -407,6 +419,27 @@ const void *dev_input(md_ctx *c, const void *p, size_t bytes, size_t stage_off, 
         return nullptr;
     }
     return s + stage_off;
+}
+
+// Host velocities (n x 3) into their place in the staging buffer on the side
+// stream, ordered after the work already on the context's stream; ev_side
+// marks the copy's end.
+md_status copy_velocities_beside(md_ctx *c, const double *v, const double **vdev) {
+    const size_t n = (size_t)c->n_total;
+    char *st = static_cast<char *>(stage_buffer(c, 6 * n * sizeof(double) + n * sizeof(int32_t)));
+    if (!st) return fail(c, MD_ERR_NOMEM, "staging allocation failed");
+    if (!c->side) {
+        CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming));
+    }
+    double *dst = reinterpret_cast<double *>(st) + 3 * n;
+    CK(cudaEventRecord(c->ev_main, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_main, 0));
+    CK(cudaMemcpyAsync(dst, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->side));
+    CK(cudaEventRecord(c->ev_side, c->side));
+    *vdev = dst;
+    return MD_OK;
 }
 
 // `types` from the caller are range-checked; the context's own (md_set_state
@@ -908,10 +941,26 @@ md_status md_set_state(md_ctx *c, const double *x, const double *v) {
     double *vcur = xcur + 3 * n;
     int32_t *tcur = reinterpret_cast<int32_t *>(vcur + 3 * n);
     CK(launch_get_state(c, x ? nullptr : xcur, v ? nullptr : vcur, nullptr, nullptr, nullptr, tcur));
-    md_status s = load_state(c, x ? x : xcur, v ? v : vcur, tcur, false);
+    // New positions with host velocities: the velocity copy runs on a side
+    // stream while the positions are binned, sorted and listed; the
+    // velocities go into place (by atom id) before the forces, whose thermo
+    // needs them.
+    const bool side_v = x && v && !is_device_ptr(v);
+    const double *vdev = nullptr;
+    if (side_v) {
+        md_status s = copy_velocities_beside(c, v, &vdev);
+        if (s) return s;
+    }
+    md_status s = load_state(c, x ? x : xcur, side_v ? nullptr : (v ? v : vcur), tcur, false);
     if (s) return s;
     invalidate_graphs(c);
-    s = sort_build_forces(c, true);
+    s = sort_build(c, true);
+    if (s) return s;
+    if (side_v) {
+        CK(cudaStreamWaitEvent(c->stream, c->ev_side, 0));
+        CK(launch_load_velocities(c, vdev));
+    }
+    s = forces_at_build(c);
     if (s) return s;
     return pull_thermo(c);
 }

@@ -183,6 +183,8 @@ struct md_ctx {
     void *stage = nullptr;
     size_t stage_bytes = 0;
     void *restage = nullptr;       // current state in original order (md_set_state)
+    cudaStream_t side = nullptr;   // md_set_state: host velocities copied beside the sort
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr;
     size_t restage_bytes = 0;
 
     // profiling
@@ -205,6 +207,7 @@ struct md_ctx {
 namespace mdb {
 // md_sort.cu
 cudaError_t launch_bin_sort(md_ctx *c, bool raw_input);
+cudaError_t launch_load_velocities(md_ctx *c, const double *v_aos);
 cudaError_t launch_unpack_input(md_ctx *c, const double *x_aos, const double *v_aos,
                                 const int32_t *types);
 // md_neigh.cu

@@ -302,9 +302,30 @@ __global__ void k_permute(const Box *__restrict__ boxes, const int32_t *__restri
     sh_out[k] = make_float4(s[0], s[1], s[2], __int_as_float(ty));
 }
 
+// Velocities by original id into the current slot order (md_set_state, once
+// the new positions are sorted); padding slots keep their zeros.
+__global__ void k_load_v(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
+                         int64_t ns, const int32_t *__restrict__ id,
+                         const double *__restrict__ v_aos, double *__restrict__ v) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    const Box &B = boxes[tile_box[k >> 5]];
+    if (k - B.slot_off >= B.n) return;
+    const int64_t g = id[k];
+    for (int d = 0; d < 3; ++d) v[d * ns + k] = v_aos[3 * g + d];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_load_velocities(md_ctx *c, const double *v_aos) {
+    const int t = 256;
+    k_load_v<<<blocks_for(c->ns, t), t, 0, c->stream>>>(c->dbox, c->tile_box, c->ns,
+                                                        c->id[c->oc], v_aos, c->v[c->oc]);
+    c->kernels += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_unpack_input(md_ctx *c, const double *x_aos, const double *v_aos,
                                 const int32_t *types) {

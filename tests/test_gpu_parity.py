@@ -249,3 +249,41 @@ def test_device_and_host_pointers_agree():
     sb = b.state(device="cuda")
     for k in ("x", "v", "f"):
         assert np.array_equal(sa[k], sb[k].cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_set_state_from_host_pinned_and_device(precision):
+    """md_set_state with host velocities copies them beside the re-sort and
+    puts them in place by atom id: numpy (pageable), pinned and device inputs
+    give the same state, which continues like the run it came from."""
+    s = mi.lj_melt(8, seed=15, jitter=0.1)
+    a = make(s, precision)
+    a.step(10)
+    st = a.state()
+    runs = []
+    for kind in ("numpy", "pinned", "device"):
+        b = make(s, precision)
+        if kind == "numpy":
+            b.set_state(st["x"], st["v"])
+        elif kind == "pinned":
+            b.set_state(torch.from_numpy(st["x"]).pin_memory(), torch.from_numpy(st["v"]).pin_memory())
+        else:
+            b.set_state(torch.from_numpy(st["x"]).cuda(), torch.from_numpy(st["v"]).cuda())
+        sb = b.state()
+        assert np.array_equal(sb["v"], st["v"])
+        assert np.allclose(sb["x"], st["x"], rtol=0, atol=1e-12)
+        tol = 1e-10 if precision == "fp64" else 1e-5
+        assert rel_l2(sb["f"], st["f"]) <= tol
+        b.step(10)
+        runs.append(b.state())
+    for r in runs[1:]:
+        for k in ("x", "v", "f"):
+            assert np.array_equal(r[k], runs[0][k])
+    # velocities alone, positions kept
+    c = make(s, precision)
+    v2 = -st["v"]
+    c.set_state(None, v2)
+    sc = c.state()
+    assert np.array_equal(sc["v"], v2)
+    assert np.allclose(sc["x"], oracle.wrap(s.x, s.box)[0] + 0 * sc["x"], rtol=0, atol=1e-12) or \
+        np.allclose(sc["x"] % s.box, oracle.wrap(s.x, s.box)[0], rtol=0, atol=1e-12)
