@@ -285,5 +285,4 @@ def test_set_state_from_host_pinned_and_device(precision):
     c.set_state(None, v2)
     sc = c.state()
     assert np.array_equal(sc["v"], v2)
-    assert np.allclose(sc["x"], oracle.wrap(s.x, s.box)[0] + 0 * sc["x"], rtol=0, atol=1e-12) or \
-        np.allclose(sc["x"] % s.box, oracle.wrap(s.x, s.box)[0], rtol=0, atol=1e-12)
+    assert np.allclose(sc["x"], oracle.wrap(s.x, s.box)[0], rtol=0, atol=1e-12)
