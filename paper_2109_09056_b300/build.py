@@ -1,6 +1,8 @@
 """Build libmd_b300.so (the CUDA kernels + C ABI) in-tree with nvcc for sm_103a.
 
-    python -m paper_2109_09056_b300.build [--force]
+    python paper_2109_09056_b300/build.py [--force | --ptxas]
+
+(run by path: importing the package first would load an older library).
 
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
 paper_2109_09056_b300/libmd_b300.so against the CUDA runtime.
