@@ -24,6 +24,8 @@
 // shadow; the list-side reads use the current buffers, writes go to the
 // other buffer, so the kernel never reads what it writes).
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "md_common.cuh"
 
@@ -760,38 +762,46 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         while (block > 32 && (size_t)(block / 32) * per_warp > kSmemDyn) block -= 32;
         const int warps = block / 32;
         const size_t smem = (size_t)warps * per_warp;
+        // process-wide: the kernel's shared-memory limit and the last occupancy query
+        static std::mutex mu;
         static size_t smem_set = 0, occ_smem = 0;
         static int occ = 0, occ_block = 0;
-        if (smem > smem_set) {
-            cudaError_t e = cudaFuncSetAttribute(
-                k_force_mixed<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            smem_set = smem;
+        int per_sm;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (smem > smem_set) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    k_force_mixed<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                smem_set = smem;
+            }
+            if (occ_smem != smem || occ_block != block) {
+                int per = 0;
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, k_force_mixed<T, ONE>, block, smem);
+                if (e != cudaSuccess) return e;
+                occ = per > 0 ? per : 1;
+                occ_smem = smem;
+                occ_block = block;
+            }
+            per_sm = occ;
         }
-        if (occ_smem != smem || occ_block != block) {
-            int per = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per, k_force_mixed<T, ONE>, block, smem);
-            if (e != cudaSuccess) return e;
-            occ = per > 0 ? per : 1;
-            occ_smem = smem;
-            occ_block = block;
-        }
-        int64_t grid = (int64_t)c->nsm * occ;
+        int64_t grid = (int64_t)c->nsm * per_sm;
         const int64_t need = (a.nwt + warps - 1) / warps;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
     } else {
         const int block = c->block ? std::min(c->block, kBlock64) : kBlock64;
-        static int grid_cache[9][2][kMaxWarps + 1] = {};
-        int &g = grid_cache[T][ONE][block / 32];
+        static std::atomic<int> grid_cache[kMaxWarps + 1] = {};  // per CTA size
+        int g = grid_cache[block / 32].load(std::memory_order_relaxed);
         if (g == 0) {
             int per = 0;
             cudaError_t e =
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force64<T, ONE>, block, 0);
             if (e != cudaSuccess) return e;
             g = per > 0 ? per : 1;
+            grid_cache[block / 32].store(g, std::memory_order_relaxed);
         }
         const int64_t warps_per_block = block / 32;
         int64_t grid = (int64_t)c->nsm * g;
