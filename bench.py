@@ -42,7 +42,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lj_fcc100_4m")
@@ -91,30 +91,48 @@ class Dist:
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler (every 50 ms) running during the timed region; the
+    constructor returns once the first sample is in, so the region is covered."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
+        import threading
+        self.lines = []
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "--format=csv,noheader,nounits", "-lms", "50",
                                        "-i", str(index)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 5.0 and self.p.poll() is None:
+            time.sleep(0.005)
+        self.skip = len(self.lines)  # samples taken before the timed region starts
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line)
 
     def stop(self):
         if self.p is None:
             return None
+        n_in = len(self.lines)
         self.p.terminate()
         try:
-            out, _ = self.p.communicate(timeout=5)
+            self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-            out, _ = self.p.communicate()
-        rows = [[f.strip() for f in r.split(",")] for r in out.strip().splitlines() if r.count(",") >= 8]
+            self.p.wait()
+        self.t.join(timeout=5)
+        # the samples taken while the region ran, else the one just before it
+        taken = self.lines[self.skip:n_in] or self.lines[max(0, n_in - 1):n_in]
+        rows = [[f.strip() for f in r.split(",")] for r in taken if r.count(",") >= 8]
         if not rows:
             return None
 
