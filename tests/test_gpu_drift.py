@@ -1,0 +1,42 @@
+"""Energy over the 131,072-atom melt's full run (32^3 FCC cells, T* 1.44,
+1000 NVE steps, rebuild every 20) against the FP64 oracle's run of the same
+steps: the FP64 path tracks the oracle's total energy to 1e-8 per atom at every
+logged step, the mixed path to 1e-3 per atom, and both drift like the oracle
+(the drift itself comes from the plain truncation at rc and the fixed cadence,
+so it is the same in all three runs)."""
+import numpy as np
+import pytest
+
+import md_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_util import make  # noqa: E402
+
+NSTEPS, EVERY = 1000, 50
+
+
+@pytest.fixture(scope="module")
+def reference():
+    s = mi.workload("lj_fcc32_131072")
+    r = oracle.md_run(s.x, s.v, s.types, s.box, NSTEPS)
+    return s, r.thermo[::EVERY, 2] / s.n          # total energy per atom at steps 0, 50, ...
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-3)])
+def test_energy_tracks_oracle_over_1000_steps(reference, precision, tol):
+    s, e_ref = reference
+    sysm = make(s, precision, thermo_every=EVERY)
+    sysm.step(NSTEPS)
+    log = sysm.thermo_log()
+    sysm.close()
+    assert np.array_equal(log[:, 0], np.arange(0, NSTEPS + 1, EVERY))
+    e = log[:, 3] / s.n
+    assert np.abs(e - e_ref).max() <= tol
+    drift, drift_ref = e[-1] - e[0], e_ref[-1] - e_ref[0]
+    assert abs(drift - drift_ref) <= tol
