@@ -1,9 +1,11 @@
 """Energy over the 131,072-atom melt's full run (32^3 FCC cells, T* 1.44,
 1000 NVE steps, rebuild every 20) against the FP64 oracle's run of the same
-steps: the FP64 path tracks the oracle's total energy to 1e-8 per atom at every
-logged step, the mixed path to 1e-3 per atom, and both drift like the oracle
-(the drift itself comes from the plain truncation at rc and the fixed cadence,
-so it is the same in all three runs)."""
+steps: the FP64 path tracks the oracle's total energy per atom to ~1e-12 for
+the first ~850 steps, after which the chaotic growth of the 1e-16 summation-
+order differences lets a pair near the cutoff differ and the runs separate
+(2.5e-7 at step 950 in one run), hence the 1e-6 bar; the mixed path stays
+within 1e-3 per atom; both drift like the oracle (the drift itself comes from
+the plain truncation at rc and the fixed cadence, the same in all three runs)."""
 import numpy as np
 import pytest
 
@@ -28,7 +30,7 @@ def reference():
     return s, r.thermo[::EVERY, 2] / s.n          # total energy per atom at steps 0, 50, ...
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("mixed", 1e-3)])
 def test_energy_tracks_oracle_over_1000_steps(reference, precision, tol):
     s, e_ref = reference
     sysm = make(s, precision, thermo_every=EVERY)
