@@ -318,9 +318,15 @@ def oracle_sample(sysd):
     return sysd.n * MD_PER_STEP / period, t0 + t2, oracle.num_threads(), period
 
 
-SAMPLE_NOTE = ("oracle on all {n} atoms: one re-sort + list build + forces (t0), then the same "
+SAMPLE_NOTE = ("oracle on {what}: one re-sort + list build + forces (t0), then the same "
                "plus 2 velocity-Verlet steps (t2); {w:.1f} s of CPU work; scaled to a 20-step "
                "period as t0 + 19*(t2-t0)/2")
+
+
+# The reference arm times every step on a bounded sample of the workload: the
+# same recipe at 1/8 the atoms for the 4M-atom melt (about 1 s of CPU per step,
+# so that --steps 30 --warmup 3 ends within a minute or two on the host cores).
+REFERENCE_SAMPLE = {"lj_fcc100_4m": "lj_fcc50_500k"}
 
 
 def run_reference(args, dist):
@@ -329,7 +335,7 @@ def run_reference(args, dist):
         return 0
     import md_inputs as mi
     import oracle
-    sysd = mi.workload(args.workload)
+    sysd = mi.workload(REFERENCE_SAMPLE.get(args.workload, args.workload))
     oracle.build()
     for _ in range(args.warmup):
         oracle_sample(sysd)
@@ -340,14 +346,19 @@ def run_reference(args, dist):
         work += w
     total = sum(periods)
     value = sysd.n * MD_PER_STEP * args.steps / total
+    line_atoms = mi.workload(args.workload).n if args.workload in REFERENCE_SAMPLE else sysd.n
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "atoms": sysd.n, "md_steps_per_step": MD_PER_STEP,
+            "config": {"workload": args.workload, "atoms": line_atoms,
+                       "sample_atoms": sysd.n, "md_steps_per_step": MD_PER_STEP,
                        "precision": "fp64", "rebuild_every": 20},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": SAMPLE_NOTE.format(n=sysd.n, w=work / args.steps)},
+                             "sample": SAMPLE_NOTE.format(
+                                 what=(f"all {sysd.n} atoms" if sysd.n == line_atoms else
+                                       f"a {sysd.n}-atom sample of the same recipe, each step"),
+                                 w=work / args.steps)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -547,7 +558,7 @@ def run_ours(args, dist):
         oracle.build()
         v_cpu, work, cores, _ = oracle_sample(sysd)
         cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": SAMPLE_NOTE.format(n=n, w=work)}
+               "sample": SAMPLE_NOTE.format(what=f"all {n} atoms", w=work)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
