@@ -25,10 +25,9 @@
 // difference), so r^2 near rs^2 is off by at most 2 sqrt(3) rs 6.25 u rs plus
 // two FP32 roundings of r^2, < 24 u rs^2.  Candidates with FP32 r^2 outside
 // [rs^2 - band, rs^2 + band], band = 3e-5 rs^2, are decided in FP32; the few
-// inside are re-tested with the exact FP64 rule on the wrapped FP64
-// positions.  When an axis has only 2 cells, the -1 and +1 stencil slots hold
-// the same cell under two images; only one image can lie within rs
-// (L > 2 rs), and the FP64 re-test checks that the slot's image is the
+// inside are re-tested with the exact FP64 rule on the wrapped FP64 positions.  When an axis has only 2 cells, the -1 and +1 stencil
+// slots hold the same cell under two images; only one image can lie within
+// rs (L > 2 rs), and the FP64 re-test checks that the slot's image is the
 // nearest one.
 #include <algorithm>
 
@@ -39,9 +38,9 @@ namespace {
 
 constexpr int kWarps = 4;       // cells per CTA (one warp each)
 // Candidates staged per warp per window: small enough that eight 4-warp CTAs
-// fit in shared memory (B300, 4M atoms: 640 -> 3.18 ms per build, 384 or 320
-// -> 2.75 ms; a typical stencil then takes two windows).
-constexpr int kCand = 320;
+// fit in shared memory (B300, 4M atoms: 640 -> 3.18 ms per build, 384 -> 2.75
+// ms; a typical stencil then takes two windows).
+constexpr int kCand = 384;
 
 struct BuildArgs {
     const Box *boxes;
@@ -79,7 +78,7 @@ __device__ __forceinline__ bool exact_test(const BuildArgs &a, const Box &B, int
 }
 
 // Resident CTAs per SM the build's register budget is sized for (8: 64
-// registers; with kCand 320 the shared memory of 8 CTAs fits too).
+// registers, no spills; with kCand 384 the shared memory of 8 CTAs fits too).
 #ifndef MD_BUILD_MINB
 #define MD_BUILD_MINB 8
 #endif
@@ -92,9 +91,6 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
     __shared__ int64_t s_start[kWarps][27];
     __shared__ int32_t s_pref[kWarps][28];
     __shared__ __align__(16) float4 hpos[kWarps][32];
-    // T == 4: the 16-byte group of row entries a lane is filling
-    __shared__ __align__(16) uint4 grp4[kWarps][32];
-    uint32_t(*grp)[32][4] = reinterpret_cast<uint32_t(*)[32][4]>(grp4);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * kWarps + w;
     if (c >= a.ncell) return;  // whole warp
@@ -166,15 +162,7 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
                 const uint32_t meta = __float_as_uint(cand[w][gb + k].w);
                 if (meta != self_meta) {
                     const unsigned uc = (unsigned)cnt;
-                    if constexpr (T == 4) {
-                        // a row's 4 consecutive entries are 16 contiguous bytes:
-                        // gather them in shared memory, store each group at once
-                        grp[w][lane][uc & 3u] = meta;
-                        if ((uc & 3u) == 3u && cnt < a.pad)
-                            *reinterpret_cast<uint4 *>(rowp + (uc >> 2) * 32u) = grp4[w][lane];
-                    } else {
-                        if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = meta;
-                    }
+                    if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = meta;
                     ++cnt;
                 }
             }
@@ -239,20 +227,8 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
             if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
             // the row's slots past its count hold the sentinel entry
             const uint32_t sent = sentinel_entry(a.ns);
-            unsigned k = (unsigned)cnt;
-            if constexpr (T == 4) {
-                if ((k & 3u) != 0u) {  // the open group: its entries, then sentinels
-                    for (unsigned q = k & 3u; q < 4u; ++q) grp[w][lane][q] = sent;
-                    if (cnt < a.pad)
-                        *reinterpret_cast<uint4 *>(rowp + (k >> 2) * 32u) = grp4[w][lane];
-                    k = (k | 3u) + 1u;
-                }
-                for (; k < (unsigned)a.pad; k += 4u)
-                    *reinterpret_cast<uint4 *>(rowp + (k >> 2) * 32u) =
-                        make_uint4(sent, sent, sent, sent);
-            } else {
-                for (; k < (unsigned)a.pad; ++k) rowp[(k / T) * 32u + k % T] = sent;
-            }
+            for (unsigned k = (unsigned)cnt; k < (unsigned)a.pad; ++k)
+                rowp[(k / T) * 32u + k % T] = sent;
         }
         const int mx = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
         const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt : 0u);
