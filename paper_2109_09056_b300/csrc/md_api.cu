@@ -66,7 +66,7 @@ void free_all(md_ctx *c) {
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
     F(c->tpart); F(c->tbox); F(c->fpart); F(c->tlog); F(c->dscratch); F(c->stage);
-    F(c->restage); F(c->scan_part);
+    F(c->restage); F(c->scan_part); F(c->ctab);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -363,6 +363,16 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     CK(cudaMemset(c->count, 0, (size_t)c->ncell_tot * sizeof(int32_t)));
     CK(dalloc(&c->cstart, (size_t)c->ncell_tot + 1));
     CK(dalloc(&c->scan_part, (size_t)c->ncell_tot / 1024 + 1));
+    // cell centres (c + 1/2) h per box and axis, rounded as the device would
+    std::vector<double> ctab;
+    for (int b = 0; b < nbox; ++b) {
+        Box &B = c->hbox[b];
+        B.ctab = (int32_t)ctab.size();
+        for (int d = 0; d < 3; ++d)
+            for (int k = 0; k < B.nc[d]; ++k) ctab.push_back(((double)k + 0.5) * B.h[d]);
+    }
+    CK(dalloc(&c->ctab, ctab.size()));
+    CK(cudaMemcpy(c->ctab, ctab.data(), sizeof(double) * ctab.size(), cudaMemcpyHostToDevice));
     CK(dalloc(&c->dbox, (size_t)nbox));
     CK(cudaMemcpy(c->dbox, c->hbox.data(), sizeof(Box) * nbox, cudaMemcpyHostToDevice));
     std::vector<int32_t> tb(ns / 32), cb((size_t)c->ncell_tot);

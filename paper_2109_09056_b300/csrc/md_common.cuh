@@ -68,7 +68,7 @@ struct Box {
     int32_t slot_off; // first slot
     int32_t n;        // atoms
     int32_t npad;     // slots (multiple of 32)
-    int32_t pad_;
+    int32_t ctab;     // offset of this box's cell centres in md_ctx::ctab
     int64_t atom_base;  // sum of n over earlier boxes
 };
 
@@ -103,8 +103,11 @@ constexpr uint32_t kCodeZero = 13;
 
 // The centre of cell (cx, cy, cz) along axis d, computed identically wherever
 // an FP64 position is reconstructed as O + r.
-__device__ __forceinline__ double cell_centre(int c, double h) {
-    return __dmul_rn((double)c + 0.5, h);
+// Centre of cell c along axis d of box B: (c + 1/2) h_d, each rounded once,
+// tabulated on the host (md_ctx::ctab: per box the nc_x, nc_y, nc_z centres).
+__device__ __forceinline__ double cell_centre(const double *__restrict__ ctab, const Box &B, int d,
+                                              int c) {
+    return __ldg(ctab + B.ctab + (d == 0 ? 0 : (d == 1 ? B.nc[0] : B.nc[0] + B.nc[1])) + c);
 }
 
 __device__ __forceinline__ void unpack_cell(int32_t p, int &cx, int &cy, int &cz) {
@@ -146,6 +149,7 @@ struct md_ctx {
     int32_t *cell = nullptr, *rank = nullptr, *perm = nullptr, *ptmp = nullptr;
     int32_t *count = nullptr, *cstart = nullptr, *nn = nullptr;
     int32_t *scan_part = nullptr;  // per-block sums of the cell-count scan
+    double *ctab = nullptr;        // cell centres of every box and axis (Box::ctab)
     uint32_t *nbr = nullptr;
     size_t nbr_words = 0;
     mdb::Box *dbox = nullptr;

@@ -687,7 +687,8 @@ __global__ void k_finalize(int split, const double *__restrict__ fpart,
 }
 
 __global__ void k_get_state(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
-                            int64_t ns, const double *__restrict__ r,
+                            const double *__restrict__ ctab, int64_t ns,
+                            const double *__restrict__ r,
                             const int32_t *__restrict__ cellc, const double *__restrict__ v,
                             const double *__restrict__ f, const int32_t *__restrict__ img,
                             const int32_t *__restrict__ id, double *__restrict__ xo,
@@ -703,7 +704,7 @@ __global__ void k_get_state(const Box *__restrict__ boxes, const int32_t *__rest
     int cc[3];
     unpack_cell(cellc[k], cc[0], cc[1], cc[2]);
     for (int d = 0; d < 3; ++d) {
-        if (xo) xo[3 * g + d] = __dadd_rn(cell_centre(cc[d], B.h[d]), r[d * ns + k]);
+        if (xo) xo[3 * g + d] = __dadd_rn(cell_centre(ctab, B, d, cc[d]), r[d * ns + k]);
         if (vo) vo[3 * g + d] = v[d * ns + k];
         if (fo) fo[3 * g + d] = f[d * ns + k];
         if (imgo) imgo[3 * g + d] = img[d * ns + k];
@@ -884,7 +885,7 @@ cudaError_t launch_get_state(md_ctx *c, double *x_aos, double *v_aos, double *f_
                              int32_t *img_aos, int32_t *ids, int32_t *types) {
     const int t = 256;
     k_get_state<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
-        c->dbox, c->tile_box, c->ns, c->r[c->pc], c->cellc[c->oc], c->v[c->oc], c->f,
+        c->dbox, c->tile_box, c->ctab, c->ns, c->r[c->pc], c->cellc[c->oc], c->v[c->oc], c->f,
         c->img[c->oc], c->id[c->oc], x_aos, v_aos, f_aos, img_aos, ids, c->type[c->oc], types);
     return cudaGetLastError();
 }

@@ -55,7 +55,8 @@ __global__ void k_unpack(const Box *__restrict__ boxes, const int32_t *__restric
 }
 
 __global__ void k_bin(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
-                      int64_t ns, int raw, const double *__restrict__ r,
+                      const double *__restrict__ ctab, int64_t ns, int raw,
+                      const double *__restrict__ r,
                       const double *__restrict__ xraw, const int32_t *__restrict__ cellc,
                       int32_t *__restrict__ img, const double *__restrict__ rbuild,
                       double *__restrict__ xw, int32_t *__restrict__ cell,
@@ -77,7 +78,7 @@ __global__ void k_bin(const Box *__restrict__ boxes, const int32_t *__restrict__
             unpack_cell(cellc[i], cc[0], cc[1], cc[2]);
             for (int d = 0; d < 3; ++d) {
                 const double rd = r[d * ns + i];
-                x[d] = __dadd_rn(cell_centre(cc[d], B.h[d]), rd);
+                x[d] = __dadd_rn(cell_centre(ctab, B, d, cc[d]), rd);
                 const float dd = (float)(rd - rbuild[d * ns + i]);
                 disp2 += dd * dd;
             }
@@ -90,7 +91,10 @@ __global__ void k_bin(const Box *__restrict__ boxes, const int32_t *__restrict__
             for (int d = 0; d < 3; ++d) {
                 const double L = B.L[d];
                 double w;
-                if (x[d] >= 0.0 && x[d] < L) {
+                // 0 <= x < L by the bit patterns (non-negative doubles order as
+                // integers; -0.0 takes the general rule, which gives +0.0)
+                const long long xb = __double_as_longlong(x[d]);
+                if (xb >= 0 && xb < __double_as_longlong(L)) {
                     // inside the box: the general rule below gives w = x, k = 0
                     // (x/L may round to 1, then w = (x - L) + L = x exactly);
                     // + 0.0 maps -0.0 to +0.0 as it does
@@ -240,7 +244,8 @@ __global__ void k_segsort(const Box *__restrict__ boxes, const int32_t *__restri
 }
 
 __global__ void k_permute(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
-                          int64_t ns, const int32_t *__restrict__ perm,
+                          const double *__restrict__ ctab, int64_t ns,
+                          const int32_t *__restrict__ perm,
                           const int32_t *__restrict__ cell, const double *__restrict__ xw,
                           const double *__restrict__ v_in, const int32_t *__restrict__ t_in,
                           const int32_t *__restrict__ id_in, const int32_t *__restrict__ img_in,
@@ -287,7 +292,7 @@ __global__ void k_permute(const Box *__restrict__ boxes, const int32_t *__restri
     float s[3];
     for (int d = 0; d < 3; ++d) {
         double w = xw[d * ns + old];
-        double rd = __dsub_rn(w, cell_centre(cc[d], B.h[d]));
+        double rd = __dsub_rn(w, cell_centre(ctab, B, d, cc[d]));
         r_out[d * ns + k] = rd;
         rbuild[d * ns + k] = rd;
         xws[d * ns + k] = w;
@@ -343,7 +348,7 @@ cudaError_t launch_bin_sort(md_ctx *c, bool raw_input) {
     cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(int32_t) * (size_t)c->ncell_tot, c->stream);
     if (e != cudaSuccess) return e;
     k_bin<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
-        c->dbox, c->tile_box, c->ns, raw_input ? 1 : 0, c->r[pc], c->xraw, c->cellc[oc],
+        c->dbox, c->tile_box, c->ctab, c->ns, raw_input ? 1 : 0, c->r[pc], c->xraw, c->cellc[oc],
         c->img[oc], c->rbuild, c->xw, c->cell, c->rank, c->count, c->dflags);
     const unsigned nsb = blocks_for(c->ncell_tot, kScanCells);
     k_scan_sum<<<nsb, kScanThreads, 0, c->stream>>>(c->count, c->ncell_tot, c->scan_part,
@@ -357,7 +362,7 @@ cudaError_t launch_bin_sort(md_ctx *c, bool raw_input) {
     k_segsort<<<blocks_for((int64_t)c->ncell_tot * 32, t), t, 0, c->stream>>>(
         c->dbox, c->cell_box, c->ncell_tot, c->cstart, c->ptmp, c->perm, c->dflags);
     k_permute<<<blocks_for(c->ns, t), t, 0, c->stream>>>(
-        c->dbox, c->tile_box, c->ns, c->perm, c->cell, c->xw, c->v[oc], c->type[oc], c->id[oc],
+        c->dbox, c->tile_box, c->ctab, c->ns, c->perm, c->cell, c->xw, c->v[oc], c->type[oc], c->id[oc],
         c->img[oc], c->r[pc], c->v[oc ^ 1], c->type[oc ^ 1], c->id[oc ^ 1], c->img[oc ^ 1],
         c->cellc[oc ^ 1], c->cellc[oc], c->sh[pc], c->rbuild, c->xws, c->nn, c->dflags);
     c->oc ^= 1;
