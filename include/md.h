@@ -23,8 +23,10 @@
  *    library re-sorts atoms into cell order internally; only md_get_state's
  *    ids, md_get_permutation and md_get_neighbors expose that internal order.
  *  - All device work is enqueued on the CUDA stream given at creation
- *    (NULL = legacy default stream).  Calls that return values to the host
- *    (getters, md_step, md_compute_forces) synchronise that stream.
+ *    (NULL = legacy default stream); md_set_state alone copies host
+ *    velocities on a library-owned side stream, ordered after that stream and
+ *    before the work that needs them by events.  Calls that return values to
+ *    the host (getters, md_step, md_compute_forces) synchronise that stream.
  *  - A context is not thread-safe; distinct contexts are independent.
  *  - Units are reduced LJ units (k_B = 1).  The box is orthorhombic with its
  *    origin at 0 and periodic on all axes.
