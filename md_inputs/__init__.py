@@ -179,3 +179,58 @@ def workload(name: str) -> LJSystem:
     if name == "lj_2type_fcc20_32000":
         return two_type_melt(20, seed=7)
     raise KeyError(name)
+
+
+# ---- charged inputs (Ewald / SPME long-range path) ------------------------
+
+def neutral_charges(n: int, rng: np.random.Generator, q: float = 1.0) -> np.ndarray:
+    """n charges of +q and -q, floor(n/2) of each sign plus one 0 if n is odd,
+    assigned to atoms in a random order (a neutral random ionic mixture)."""
+    c = np.zeros(n)
+    c[: n // 2] = q
+    c[n // 2: 2 * (n // 2)] = -q
+    return np.ascontiguousarray(c[rng.permutation(n)])
+
+
+def rocksalt(nc: int, r0: float = 1.0) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Rock-salt (NaCl) crystal: a simple-cubic nc^3 lattice of spacing r0
+    (nc even) with charges (-1)^(i+j+k).  Returns positions, charges, box."""
+    if nc % 2:
+        raise ValueError("nc must be even for a periodic rock-salt box")
+    g = np.arange(nc)
+    i, j, k = np.meshgrid(g, g, g, indexing="ij")
+    x = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1) * float(r0)
+    q = np.where((i + j + k).ravel() % 2 == 0, 1.0, -1.0)
+    return np.ascontiguousarray(x, dtype=np.float64), q, np.full(3, nc * float(r0))
+
+
+@dataclass
+class ChargedSystem:
+    """An LJ melt whose atoms also carry charges, with the Ewald parameters
+    of the recipe (splitting alpha, real-space cutoff, grid, spline order)."""
+    lj: LJSystem
+    q: np.ndarray
+    alpha: float
+    rc: float
+    K: tuple
+    order: int
+
+
+def charged_melt(ncells: int, seed: int, K: int, order: int = 4, jitter: float = 0.05,
+                 alpha: float = 1.25, rc: float = RC) -> ChargedSystem:
+    """The LJ melt recipe (FCC at rho 0.8442, T 1.44, jitter in sigma) with
+    neutral random +-1 charges; alpha rc = 3.125 (erfc(alpha rc) ~ 1e-5)."""
+    s = lj_melt(ncells, seed=seed, jitter=jitter)
+    q = neutral_charges(s.n, np.random.default_rng(seed + 1000))
+    return ChargedSystem(lj=s, q=q, alpha=alpha, rc=rc, K=(K, K, K), order=order)
+
+
+def charged_workload(name: str) -> ChargedSystem:
+    """The named charged workloads (grid K^3 chosen for ~0.44 sigma spacing)."""
+    if name == "coulomb_fcc10_4000":
+        return charged_melt(10, seed=21, K=40)
+    if name == "coulomb_fcc50_500k":
+        return charged_melt(50, seed=23, K=192)
+    if name == "coulomb_fcc100_4m":
+        return charged_melt(100, seed=25, K=384)
+    raise KeyError(name)
