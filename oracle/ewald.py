@@ -121,7 +121,7 @@ def _stencil(x, box, K, n: int):
     return idx, bspline(n, t), bspline_deriv(n, t)
 
 
-def spme_reciprocal(x, q, box, alpha: float, K, n: int, chunk: int = 65536):
+def spme_reciprocal(x, q, box, alpha: float, K, n: int, chunk: int = 65536, sample=None):
     """SPME reciprocal-space energy and forces (SPME paper, Secs. 3-4), in
     the order the paper's CabanaMD section lists the steps: spread the charges
     onto Q with the order-n B-splines, forward 3-D FFT, multiply by theta and
@@ -129,7 +129,8 @@ def spme_reciprocal(x, q, box, alpha: float, K, n: int, chunk: int = 65536):
 
     x (n_atoms, 3) positions (any periodic image), q (n_atoms,) charges,
     box (3,) edges, K (3,) grid points per axis (K_x, K_y, K_z).
-    Returns (E_recip, F (n_atoms, 3))."""
+    Returns (E_recip, F (n_atoms, 3)); with `sample` (atom indices) the forces
+    of those atoms only (the grid always holds every charge)."""
     q = np.asarray(q, dtype=np.float64)
     K = [int(k) for k in K]
     L = np.asarray(box, dtype=np.float64)
@@ -148,16 +149,19 @@ def spme_reciprocal(x, q, box, alpha: float, K, n: int, chunk: int = 65536):
     Qh = np.fft.fftn(Q)
     E = 0.5 * float(np.sum(theta * (Qh.real ** 2 + Qh.imag ** 2)))
     dEdQ = (np.fft.ifftn(theta * Qh).real * ntot).ravel()
-    F = np.empty((N, 3))
-    for s in range(0, N, chunk):
-        idx, W, D = _stencil(np.asarray(x)[s:s + chunk], L, K, n)
+    rows = np.arange(N) if sample is None else np.asarray(sample, dtype=np.int64)
+    xr = np.asarray(x, dtype=np.float64)[rows]
+    qr = q[rows]
+    F = np.empty((len(rows), 3))
+    for s in range(0, len(rows), chunk):
+        idx, W, D = _stencil(xr[s:s + chunk], L, K, n)
         flat = ((idx[:, 2, :, None, None] * K[1] + idx[:, 1, None, :, None]) * K[0]
                 + idx[:, 0, None, None, :])
         ph = dEdQ[flat]
         gx = (W[:, 2, :, None, None] * W[:, 1, None, :, None] * D[:, 0, None, None, :] * ph).sum((1, 2, 3))
         gy = (W[:, 2, :, None, None] * D[:, 1, None, :, None] * W[:, 0, None, None, :] * ph).sum((1, 2, 3))
         gz = (D[:, 2, :, None, None] * W[:, 1, None, :, None] * W[:, 0, None, None, :] * ph).sum((1, 2, 3))
-        F[s:s + chunk] = -q[s:s + chunk, None] * np.stack(
+        F[s:s + chunk] = -qr[s:s + chunk, None] * np.stack(
             [gx * (K[0] / L[0]), gy * (K[1] / L[1]), gz * (K[2] / L[2])], axis=1)
     return E, F
 
@@ -189,13 +193,18 @@ def ewald_reciprocal(x, q, box, alpha: float, kmax, chunk: int = 2048):
     return E, F
 
 
+def _min_image(d, L):
+    """Separations of wrapped positions folded once: d > L/2 -> d - L,
+    d < -L/2 -> d + L."""
+    return np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+
+
 def _real_rows(xw, q, L, alpha: float, rc: float, rows):
     """Real-space forces and half-energies of atoms `rows` against every other
     atom, minimum image on wrapped positions (a separation d > L/2 is taken
     as d - L, d < -L/2 as d + L), pairs with r^2 < rc^2."""
     xi = xw[rows]
-    d = xw[None, :, :] - xi[:, None, :]                 # x_j - x_i
-    d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    d = _min_image(xw[None, :, :] - xi[:, None, :], L)  # x_j - x_i
     r2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
     mask = r2 < rc * rc
     mask[np.arange(len(rows)), rows] = False
@@ -231,16 +240,21 @@ def ewald_real(x, q, box, alpha: float, rc: float, block: int = 256):
     return E, F
 
 
-def ewald_real_sample(x, q, box, alpha: float, rc: float, sample, block: int = 8):
-    """Real-space forces of the atoms in `sample` only (brute force over all
-    atoms, as ewald_real)."""
+def ewald_real_sample(x, q, box, alpha: float, rc: float, sample):
+    """Real-space forces of the atoms in `sample` only: for each, the same
+    minimum-image rule and pair terms as ewald_real over every other atom
+    (atoms farther than rc along some axis are skipped first)."""
     L = np.asarray(box, dtype=np.float64)
     xw = wrap(x, L)
     q = np.asarray(q, dtype=np.float64)
     sample = np.asarray(sample, dtype=np.int64)
     F = np.zeros((len(sample), 3))
-    for s in range(0, len(sample), block):
-        F[s:s + block], _ = _real_rows(xw, q, L, alpha, rc, sample[s:s + block])
+    for k, i in enumerate(sample):
+        d = _min_image(xw - xw[i], L)
+        near = np.flatnonzero(np.all(np.abs(d) < rc, axis=1))
+        near = near[near != i]
+        F[k], _ = _real_rows(np.vstack([xw[i:i + 1], xw[near]]),
+                             np.concatenate([q[i:i + 1], q[near]]), L, alpha, rc, np.array([0]))
     return F
 
 

@@ -1,4 +1,5 @@
-"""ctypes marshalling for libmd_b300.so (the C ABI declared in include/md.h).
+"""ctypes marshalling for libmd_b300.so (the C ABI declared in include/md.h and
+include/md_spme.h).
 
 Argument marshalling only: every step of the MD path runs in the library's
 CUDA kernels.  There is no CPU fallback: importing this module raises if the
@@ -59,7 +60,13 @@ class md_thermo(C.Structure):
                 "pad": self.pad, "builds": self.builds, "dangerous_builds": self.dangerous_builds}
 
 
-# Exported symbols and their signatures (kept in the order of include/md.h).
+class md_spme_params(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("rc", C.c_double), ("K", C.c_int32 * 3),
+                ("order", C.c_int32)]
+
+
+# Exported symbols and their signatures (kept in the order of include/md.h,
+# then include/md_spme.h).
 P = C.c_void_p
 SIGNATURES = {
     "md_params_default": ([C.POINTER(md_params)], None),
@@ -89,6 +96,14 @@ SIGNATURES = {
     "md_batch_thermo": ([P, P], C.c_int),
     "md_info": ([P, C.POINTER(C.c_int32), C.POINTER(C.c_int64)], C.c_int),
     "md_bin_sort_noalloc": ([C.POINTER(md_box), C.c_int64, P, C.c_double, P, P], C.c_int),
+    # include/md_spme.h
+    "md_spme_create": ([P, P, C.POINTER(md_spme_params), C.POINTER(P)], C.c_int),
+    "md_spme_set_charges": ([P, P], C.c_int),
+    "md_spme_compute": ([P, P, P], C.c_int),
+    "md_spme_profile": ([P, C.c_int32], C.c_int),
+    "md_spme_profile_read": ([P, P], C.c_int),
+    "md_spme_last_error": ([P], C.c_char_p),
+    "md_spme_destroy": ([P], None),
 }
 
 
@@ -118,4 +133,10 @@ class MDError(RuntimeError):
 def check(status: int, ctx=None) -> None:
     if status != MD_OK:
         msg = lib.md_last_error(ctx)
+        raise MDError(status, msg.decode() if msg else "")
+
+
+def check_spme(status: int, solver=None) -> None:
+    if status != MD_OK:
+        msg = lib.md_spme_last_error(solver)
         raise MDError(status, msg.decode() if msg else "")

@@ -1,5 +1,6 @@
-"""Python binding of the C ABI (include/md.h), one function per C entry point
-with the same name, plus the ``MDSystem`` convenience wrapper.
+"""Python binding of the C ABI (include/md.h, include/md_spme.h), one function
+per C entry point with the same name, plus the ``MDSystem`` and ``SPME``
+convenience wrappers.
 
 Arrays may be numpy arrays (host) or torch tensors (host or CUDA); device
 tensors are passed to the library as device pointers, so no copy happens on
@@ -14,7 +15,7 @@ from typing import Optional
 import numpy as np
 
 from . import _native as N
-from ._native import check, lib
+from ._native import check, check_spme, lib
 
 try:
     import torch
@@ -376,3 +377,91 @@ class MDSystem:
 
     def close(self):
         md_destroy(self.ctx)
+
+
+# ---- long-range Coulomb (include/md_spme.h) ----------------------------------
+
+class Spme:
+    """Owns an md_spme*; destroyed with md_spme_destroy.  Holds the context
+    (which must outlive the solver)."""
+
+    def __init__(self, handle: C.c_void_p, ctx: Ctx):
+        self.handle = handle
+        self.ctx = ctx
+
+    def __del__(self):
+        try:
+            md_spme_destroy(self)
+        except Exception:
+            pass
+
+
+def md_spme_create(ctx: Ctx, q, alpha: float, rc: float, K, order: int = 4) -> Spme:
+    p = N.md_spme_params()
+    p.alpha, p.rc = float(alpha), float(rc)
+    Kt = (int(K),) * 3 if np.isscalar(K) else tuple(int(k) for k in K)
+    for d in range(3):
+        p.K[d] = Kt[d]
+    p.order = int(order)
+    pq, kq = _arr(q, np.float64, (ctx.n,))
+    h = C.c_void_p()
+    check_spme(lib.md_spme_create(ctx.handle, pq, C.byref(p), C.byref(h)))
+    return Spme(h, ctx)
+
+
+def md_spme_set_charges(s: Spme, q) -> None:
+    pq, kq = _arr(q, np.float64, (s.ctx.n,))
+    check_spme(lib.md_spme_set_charges(s.handle, pq), s.handle)
+
+
+def md_spme_compute(s: Spme, device=None, forces: bool = True) -> tuple:
+    """(energies, f): energies = {"real", "recip", "self", "total"} ("self"
+    includes the neutralising-background term), f (n, 3) in original atom
+    order (None if forces is False)."""
+    pf, f = _alloc((s.ctx.n, 3), np.float64, device) if forces else (None, None)
+    e = (C.c_double * 4)()
+    check_spme(lib.md_spme_compute(s.handle, pf, e), s.handle)
+    return {"real": e[0], "recip": e[1], "self": e[2], "total": e[3]}, f
+
+
+def md_spme_profile(s: Spme, on: bool = True) -> None:
+    check_spme(lib.md_spme_profile(s.handle, int(bool(on))), s.handle)
+
+
+def md_spme_profile_read(s: Spme) -> dict:
+    """Device ms of the last md_spme_compute per stage (profiling on)."""
+    ms = (C.c_double * 6)()
+    check_spme(lib.md_spme_profile_read(s.handle, ms), s.handle)
+    return dict(zip(("spread", "fft_forward", "influence", "fft_inverse", "gather", "real"),
+                    list(ms)))
+
+
+def md_spme_destroy(s: Spme) -> None:
+    if s.handle is not None and s.handle.value:
+        lib.md_spme_destroy(s.handle)
+        s.handle = C.c_void_p()
+
+
+class SPME:
+    """Smooth particle mesh Ewald Coulomb solver attached to an MDSystem
+    (one box): ``compute()`` returns the energies and forces at the system's
+    current positions."""
+
+    def __init__(self, system: "MDSystem", q, *, alpha: float, rc: float, K, order: int = 4):
+        self.system = system
+        self.solver = md_spme_create(system.ctx, q, alpha, rc, K, order)
+
+    def set_charges(self, q):
+        md_spme_set_charges(self.solver, q)
+
+    def compute(self, device=None, forces: bool = True) -> tuple:
+        return md_spme_compute(self.solver, device, forces)
+
+    def profile(self, on: bool = True):
+        md_spme_profile(self.solver, on)
+
+    def profile_read(self) -> dict:
+        return md_spme_profile_read(self.solver)
+
+    def close(self):
+        md_spme_destroy(self.solver)

@@ -5,7 +5,8 @@
 (run by path: importing the package first would load an older library).
 
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
-paper_2109_09056_b300/libmd_b300.so against the CUDA runtime.
+paper_2109_09056_b300/libmd_b300.so against the CUDA runtime and cuFFT (the
+3-D FFTs of the SPME long-range solver).
 """
 from __future__ import annotations
 
@@ -39,7 +40,7 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "md.h")]
+    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
 def up_to_date() -> bool:
@@ -68,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         objs = list(ex.map(one, _sources()))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -502,6 +502,18 @@ struct OutBuf {
 
 }  // namespace
 
+namespace mdb {
+// For solvers attached to a context (md_spme.cu): the list guarantee that
+// md_compute_forces gives (build it if the context has none), failures
+// reported in c->err.
+md_status ensure_list(md_ctx *c) {
+    if (!c->ready) return fail(c, MD_ERR_ARG, "internal: state between half-steps");
+    if (c->list_valid) return MD_OK;
+    return build_with_retry(c);
+}
+bool is_device_pointer(const void *p) { return is_device_ptr(p); }
+}  // namespace mdb
+
 md_status mdb::set_global_error(md_status s, const std::string &msg) {
     g_create_error = msg;
     return s;

