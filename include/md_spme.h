@@ -25,12 +25,13 @@
  * gradient of Q contracted with dE/dQ = inverse FFT of theta FFT(Q).
  *
  * Conventions are those of md.h (status returns, host-or-device pointers,
- * original atom order, the context's stream).  Arithmetic: the reciprocal
- * part (spread, FFT, influence, gather) is FP64 in both context precisions.
- * The real-space part follows the context's precision: FP64 for MD_FP64;
- * for MD_MIXED, FP32 pair arithmetic on the context's cell-relative shadow
- * with Kahan-compensated FP32 per-atom sums, FP64 force output and FP64
- * energy total.  The 3-D FFTs are cuFFT (double-complex, out of place).
+ * original atom order, the context's stream).  Arithmetic follows the
+ * context's precision.  MD_FP64: everything in FP64 (double-complex FFTs).
+ * MD_MIXED: reciprocal part with FP32 spline weights, an FP32 grid,
+ * single-precision FFTs and an FP32 gather; real-space pairs in FP32 on the
+ * context's cell-relative shadow with Kahan-compensated per-atom sums; energy
+ * totals accumulated in FP64 and forces returned in FP64.  The 3-D FFTs are
+ * cuFFT (real-to-complex and back, out of place).
  */
 #ifndef MD_B300_SPME_H
 #define MD_B300_SPME_H
@@ -57,13 +58,14 @@ typedef struct {
 
 /* Attaches an SPME solver to ctx, which must hold one box and outlive the
  * solver.  q: n charges (the context's n) in original atom order, host or
- * device, copied.  Allocates the grid (K_x K_y K_z FP64), its half spectrum
- * (K_z K_y (K_x/2+1) FP64 complex), the influence table theta (same size,
- * FP64, built once on the device) and two cuFFT plans on the context's stream.
+ * device, copied.  Allocates the grid (K_x K_y K_z reals), its half spectrum
+ * (K_z K_y (K_x/2+1) complex), the influence table theta (K_z K_y (K_x/2+1)
+ * reals, built once on the device), reals FP64 or FP32 by the context's
+ * precision, and two cuFFT plans on the context's stream.
  * Errors: MD_ERR_ARG (NULL pointer, batched context, parameter out of range),
  * MD_ERR_NONFINITE (a charge is NaN/Inf), MD_ERR_NOMEM, MD_ERR_CUDA (also for a
- * cuFFT failure).  On failure *out is NULL and md_last_error(NULL) holds the
- * message. */
+ * cuFFT failure).  On failure *out is NULL and md_spme_last_error(NULL) holds
+ * the message. */
 md_status md_spme_create(md_ctx *ctx, const double *q, const md_spme_params *p, md_spme **out);
 
 /* Replaces the charges (n values, original atom order, host or device). */

@@ -7,19 +7,25 @@
 // short-range neighbor list.  Definitions from Essmann et al., J. Chem. Phys.
 // 103, 8577 (1995), Secs. 2-4.
 //
+// Grid precision R follows the context: FP64 for MD_FP64 contexts; FP32 for
+// MD_MIXED (FP32 spline weights, grid, single-precision FFTs and gather, FP64
+// energy sums and force output).  B300's FP64 pipe runs at ~1/64 of FP32, and
+// a 384^3 double-precision FFT pair alone took 15 ms there, against the
+// memory-bound few tenths of a millisecond of the FP32 pair.
+//
 // One md_spme_compute is six launches on the context's stream:
 //   k_spme_spread   one thread per slot: charge of the slot's atom (gathered by
 //                   its original id), scaled fractional coordinates from the
 //                   FP64 cell-relative position, order-p spline weights by their
-//                   recursion, p^3 FP64 atomic adds into the grid Q;
+//                   recursion, p^3 atomic adds into the grid Q;
 //   k_spme_real     the real-space erfc pairs over the context's Verlet list
 //                   (same warp-transposed rows and lanes per atom as the LJ
 //                   kernels), FP64 or FP32 + Kahan by the context's precision;
-//   cufftExecD2Z    Q -> Qhat (half spectrum, K_z x K_y x (K_x/2+1));
+//   cuFFT R2C / D2Z Q -> Qhat (half spectrum, K_z x K_y x (K_x/2+1));
 //   k_spme_influence  per half-spectrum element: energy term theta |Qhat|^2
 //                   (weighted 2 for the elements that stand for a conjugate
 //                   pair), then Qhat *= theta;
-//   cufftExecZ2D    -> dE/dQ on the grid (unnormalised inverse);
+//   cuFFT C2R / Z2D -> dE/dQ on the grid (unnormalised inverse);
 //   k_spme_gather   one thread per slot: spline gradients against dE/dQ, plus the
 //                   slot's real-space force, written in original atom order;
 // then one single-CTA sum of the energy partials (fixed order, deterministic).
@@ -48,6 +54,8 @@ thread_local std::string g_spme_error;
 constexpr int kThreads = 256;       // spread / gather / influence CTAs
 constexpr int kRealBlock = 256;     // real-space CTA (8 warps)
 constexpr int kMaxGrid = 4096;
+constexpr int kRealBatch = 4;       // list entries per lane in flight (mixed real space)
+constexpr uint32_t kSelf = 0xFFFFFFFFu;  // batch slot past the row's end
 constexpr int kEvents = 7;
 
 struct Geom {
@@ -67,9 +75,10 @@ struct md_spme {
     double *q = nullptr;        // charges, original atom order (n)
     double *qs = nullptr;       // charge per slot (ns)
     float *qsf = nullptr;       // FP32 copy per slot (mixed real space)
-    double *grid = nullptr;     // Q, then dE/dQ: K_z x K_y x K_x
-    double2 *ghat = nullptr;    // half spectrum
-    double *theta = nullptr;    // influence function on the half spectrum
+    bool f32 = false;           // grid precision R: FP32 (mixed context) or FP64
+    void *grid = nullptr;       // Q, then dE/dQ: K_z x K_y x K_x of R
+    void *ghat = nullptr;       // half spectrum, complex R
+    void *theta = nullptr;      // influence function on the half spectrum, R
     double *fs = nullptr;       // real-space forces per slot, SoA 3 x ns
     double *part = nullptr;     // energy partials: real [nreal], then recip [nrecip]
     int64_t nreal = 0, nrecip = 0;
@@ -120,21 +129,21 @@ md_status sfft(md_spme *s, cufftResult r, const char *where) {
 // recursion M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) / (n - 1) from
 // M_1 = 1 on [0, 1), and M_n' (x) = M_{n-1}(x) - M_{n-1}(x - 1) (SPME paper,
 // Sec. 4), on the P values that are nonzero.
-template <int P, bool DERIV>
-__device__ __forceinline__ void bspline(double t, double (&w)[P], double (&dw)[P]) {
-    double a[P];
+template <typename R, int P, bool DERIV>
+__device__ __forceinline__ void bspline(R t, R (&w)[P], R (&dw)[P]) {
+    R a[P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) a[j] = j == 0 ? 1.0 : 0.0;
+    for (int j = 0; j < P; ++j) a[j] = j == 0 ? R(1) : R(0);
 #pragma unroll
     for (int n = 2; n <= P; ++n) {
         if (DERIV && n == P) {
 #pragma unroll
-            for (int j = 0; j < P; ++j) dw[j] = a[j] - (j ? a[j - 1] : 0.0);
+            for (int j = 0; j < P; ++j) dw[j] = a[j] - (j ? a[j - 1] : R(0));
         }
-        const double inv = 1.0 / (double)(n - 1);
+        const R inv = R(1) / R(n - 1);
 #pragma unroll
         for (int j = n - 1; j >= 0; --j)
-            a[j] = ((t + (double)j) * a[j] + ((double)(n - j) - t) * (j ? a[j - 1] : 0.0)) * inv;
+            a[j] = ((t + R(j)) * a[j] + (R(n - j) - t) * (j ? a[j - 1] : R(0))) * inv;
     }
 #pragma unroll
     for (int j = 0; j < P; ++j) w[j] = a[j];
@@ -169,11 +178,11 @@ struct AtomArgs {
     Geom g;
 };
 
-template <int P>
+template <int P, typename R>
 __global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const double *__restrict__ q_orig,
                                                           double *__restrict__ qs,
                                                           float *__restrict__ qsf,
-                                                          double *__restrict__ grid) {
+                                                          R *__restrict__ grid) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.ns) return;
     const Box &B = a.box[0];
@@ -184,21 +193,22 @@ __global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const doub
     int cc[3];
     unpack_cell(a.cellc[i], cc[0], cc[1], cc[2]);
     int ix[3][P];
-    double w[3][P], unused[P];
+    R w[3][P], unused[P];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double x = __dadd_rn(cell_centre(a.ctab, B, d, cc[d]), a.r[d * a.ns + i]);
         const double t = grid_stencil<P>(x, a.g.kl[d], a.g.Kd[d], a.g.K[d], ix[d]);
-        bspline<P, false>(t, w[d], unused);
+        bspline<R, P, false>((R)t, w[d], unused);
     }
     const int64_t Kx = a.g.K[0], Ky = a.g.K[1];
-#pragma unroll 1
+    const R qr = (R)q;
+#pragma unroll
     for (int c = 0; c < P; ++c) {
-        const double qz = q * w[2][c];
+        const R qz = qr * w[2][c];
 #pragma unroll
         for (int b = 0; b < P; ++b) {
-            const double qzy = qz * w[1][b];
-            double *row = grid + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
+            const R qzy = qz * w[1][b];
+            R *row = grid + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
 #pragma unroll
             for (int e = 0; e < P; ++e) atomicAdd(row + ix[0][e], qzy * w[0][e]);
         }
@@ -207,9 +217,9 @@ __global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const doub
 
 // Forces on the atoms: F = -q (K/L) sum over the P^3 stencil of the spline
 // gradient times dE/dQ, plus the slot's real-space force; out in original order.
-template <int P>
+template <int P, typename R>
 __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const double *__restrict__ qs,
-                                                          const double *__restrict__ dEdQ,
+                                                          const R *__restrict__ dEdQ,
                                                           const double *__restrict__ fs,
                                                           double *__restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -222,24 +232,24 @@ __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const doub
         int cc[3];
         unpack_cell(a.cellc[i], cc[0], cc[1], cc[2]);
         int ix[3][P];
-        double w[3][P], dw[3][P];
+        R w[3][P], dw[3][P];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double x = __dadd_rn(cell_centre(a.ctab, B, d, cc[d]), a.r[d * a.ns + i]);
             const double t = grid_stencil<P>(x, a.g.kl[d], a.g.Kd[d], a.g.K[d], ix[d]);
-            bspline<P, true>(t, w[d], dw[d]);
+            bspline<R, P, true>((R)t, w[d], dw[d]);
         }
         const int64_t Kx = a.g.K[0], Ky = a.g.K[1];
-        double gx = 0.0, gy = 0.0, gz = 0.0;
-#pragma unroll 1
+        R gx = 0, gy = 0, gz = 0;
+#pragma unroll
         for (int c = 0; c < P; ++c) {
 #pragma unroll
             for (int b = 0; b < P; ++b) {
-                const double *row = dEdQ + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
-                double sd = 0.0, sw = 0.0;
+                const R *row = dEdQ + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
+                R sd = 0, sw = 0;
 #pragma unroll
                 for (int e = 0; e < P; ++e) {
-                    const double ph = __ldg(row + ix[0][e]);
+                    const R ph = __ldg(row + ix[0][e]);
                     sd = fma(dw[0][e], ph, sd);
                     sw = fma(w[0][e], ph, sw);
                 }
@@ -248,9 +258,9 @@ __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const doub
                 gz = fma(dw[2][c] * w[1][b], sw, gz);
             }
         }
-        fr[0] = -q * a.g.kl[0] * gx;
-        fr[1] = -q * a.g.kl[1] * gy;
-        fr[2] = -q * a.g.kl[2] * gz;
+        fr[0] = -q * a.g.kl[0] * (double)gx;
+        fr[1] = -q * a.g.kl[1] * (double)gy;
+        fr[2] = -q * a.g.kl[2] * (double)gz;
     }
     const int64_t g = a.id[i];
 #pragma unroll
@@ -278,19 +288,24 @@ __device__ __forceinline__ void cta_sum_to(double v, double *out) {
     }
 }
 
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
 // Half-spectrum element h = (m_z K_y + m_y) Kh + m_x: energy term and Qhat *= theta.
-__global__ void __launch_bounds__(kThreads) k_spme_influence(double2 *__restrict__ ghat,
-                                                             const double *__restrict__ theta,
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_spme_influence(typename Cplx<R>::T *__restrict__ ghat,
+                                                             const R *__restrict__ theta,
                                                              int64_t nhalf, int Kh, int Kx,
                                                              double *__restrict__ part) {
     double e = 0.0;
     for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < nhalf;
          h += (int64_t)gridDim.x * blockDim.x) {
         const int mx = (int)(h % Kh);
-        const double wgt = (mx == 0 || 2 * mx == Kx) ? 1.0 : 2.0;
-        const double th = theta[h];
-        double2 v = ghat[h];
-        e += wgt * th * (v.x * v.x + v.y * v.y);
+        const R wgt = (mx == 0 || 2 * mx == Kx) ? R(1) : R(2);
+        const R th = theta[h];
+        auto v = ghat[h];
+        e += (double)(wgt * th * (v.x * v.x + v.y * v.y));
         v.x *= th;
         v.y *= th;
         ghat[h] = v;
@@ -300,7 +315,8 @@ __global__ void __launch_bounds__(kThreads) k_spme_influence(double2 *__restrict
 
 // theta(m) = B(m) exp(-pi^2 |m|^2 / alpha^2) / (pi V |m|^2), theta(0) = 0, on
 // the half spectrum; bmod holds |b_x|^2 (K_x), |b_y|^2 (K_y), |b_z|^2 (K_z).
-__global__ void k_spme_theta(double *__restrict__ theta, const double *__restrict__ bmod, Geom g,
+template <typename R>
+__global__ void k_spme_theta(R *__restrict__ theta, const double *__restrict__ bmod, Geom g,
                              double Lx, double Ly, double Lz, double alpha, int64_t nhalf) {
     const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (h >= nhalf) return;
@@ -313,12 +329,12 @@ __global__ void k_spme_theta(double *__restrict__ theta, const double *__restric
     const double ux = mx / Lx, uy = sy / Ly, uz = sz / Lz;
     const double msq = ux * ux + uy * uy + uz * uz;
     if (h == 0) {
-        theta[h] = 0.0;
+        theta[h] = R(0);
         return;
     }
     const double pi = 3.141592653589793;
     const double B = bmod[mx] * bmod[g.K[0] + my] * bmod[g.K[0] + g.K[1] + mz];
-    theta[h] = B * exp(-pi * pi * msq / (alpha * alpha)) / (pi * (Lx * Ly * Lz) * msq);
+    theta[h] = (R)(B * exp(-pi * pi * msq / (alpha * alpha)) / (pi * (Lx * Ly * Lz) * msq));
 }
 
 struct RealArgs {
@@ -373,25 +389,39 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
             const float4 si = a.sh[i];
             const float qi = a.qsf[i];
             float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
-            for (int k = 0; k < nq; ++k) {
-                const uint32_t e = __ldg(row + (size_t)k * 32);
-                const uint32_t j = e & MD_IDX_MASK;
-                const int cd = 3 * (int)(e >> MD_IDX_BITS);
-                const float4 sj = __ldg(a.sh + j);
-                const float dx = (sj.x + s_offf[cd]) - si.x;
-                const float dy = (sj.y + s_offf[cd + 1]) - si.y;
-                const float dz = (sj.z + s_offf[cd + 2]) - si.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < a.rc2f) {
-                    const float qq = qi * __ldg(a.qsf + j);
-                    const float rinv = rsqrtf(r2);
-                    const float er = erfcf(a.alphaf * (r2 * rinv));
-                    const float ex = expf(-(a.alphaf * a.alphaf) * r2);
-                    const float g = qq * fmaf(er, rinv, a.c2af * ex) * (rinv * rinv);
-                    kahan_add(fx, cx, -g * dx);
-                    kahan_add(fy, cy, -g * dy);
-                    kahan_add(fz, cz, -g * dz);
-                    kahan_add(pe, cp, 0.5f * qq * er * rinv);
+            // kRealBatch entries per lane at a time: their list words, then
+            // their shadows and charges, are all in flight before the math
+            for (int k0 = 0; k0 < nq; k0 += kRealBatch) {
+                uint32_t e[kRealBatch];
+#pragma unroll
+                for (int u = 0; u < kRealBatch; ++u)
+                    e[u] = k0 + u < nq ? __ldg(row + (size_t)(k0 + u) * 32) : kSelf;
+                float4 sj[kRealBatch];
+                float qj[kRealBatch];
+#pragma unroll
+                for (int u = 0; u < kRealBatch; ++u) {
+                    const uint32_t j = e[u] == kSelf ? (uint32_t)i : (e[u] & MD_IDX_MASK);
+                    sj[u] = __ldg(a.sh + j);
+                    qj[u] = e[u] == kSelf ? 0.f : __ldg(a.qsf + j);
+                }
+#pragma unroll
+                for (int u = 0; u < kRealBatch; ++u) {
+                    const int cd = e[u] == kSelf ? 3 * (int)kCodeZero : 3 * (int)(e[u] >> MD_IDX_BITS);
+                    const float dx = (sj[u].x + s_offf[cd]) - si.x;
+                    const float dy = (sj[u].y + s_offf[cd + 1]) - si.y;
+                    const float dz = (sj[u].z + s_offf[cd + 2]) - si.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (qj[u] != 0.f && r2 < a.rc2f) {
+                        const float qq = qi * qj[u];
+                        const float rinv = rsqrtf(r2);
+                        const float er = erfcf(a.alphaf * (r2 * rinv));
+                        const float ex = expf(-(a.alphaf * a.alphaf) * r2);
+                        const float g = qq * fmaf(er, rinv, a.c2af * ex) * (rinv * rinv);
+                        kahan_add(fx, cx, -g * dx);
+                        kahan_add(fy, cy, -g * dy);
+                        kahan_add(fz, cz, -g * dz);
+                        kahan_add(pe, cp, 0.5f * qq * er * rinv);
+                    }
                 }
             }
             F[0] = (double)(fx - cx);
@@ -495,25 +525,33 @@ cudaError_t launch_real(int T, const RealArgs &ra, int blocks, cudaStream_t st) 
     }
 }
 
-template <int P>
+template <int P, typename R>
 cudaError_t launch_atoms(bool gather, const AtomArgs &aa, const double *q_orig, double *qs,
-                         float *qsf, double *grid, const double *fs, double *out, cudaStream_t st) {
+                         float *qsf, void *grid, const double *fs, double *out, cudaStream_t st) {
     const int blocks = (int)((aa.ns + kThreads - 1) / kThreads);
     if (gather)
-        k_spme_gather<P><<<blocks, kThreads, 0, st>>>(aa, qs, grid, fs, out);
+        k_spme_gather<P, R><<<blocks, kThreads, 0, st>>>(aa, qs, (const R *)grid, fs, out);
     else
-        k_spme_spread<P><<<blocks, kThreads, 0, st>>>(aa, q_orig, qs, qsf, grid);
+        k_spme_spread<P, R><<<blocks, kThreads, 0, st>>>(aa, q_orig, qs, qsf, (R *)grid);
     return cudaGetLastError();
 }
 
+template <typename R>
 cudaError_t launch_atoms_p(int p, bool gather, const AtomArgs &aa, const double *q_orig, double *qs,
-                           float *qsf, double *grid, const double *fs, double *out, cudaStream_t st) {
+                           float *qsf, void *grid, const double *fs, double *out, cudaStream_t st) {
     switch (p) {
-        case 4: return launch_atoms<4>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
-        case 6: return launch_atoms<6>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
-        case 8: return launch_atoms<8>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 4: return launch_atoms<4, R>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 6: return launch_atoms<6, R>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 8: return launch_atoms<8, R>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_atoms_any(bool f32, int p, bool gather, const AtomArgs &aa, const double *q_orig,
+                             double *qs, float *qsf, void *grid, const double *fs, double *out,
+                             cudaStream_t st) {
+    return f32 ? launch_atoms_p<float>(p, gather, aa, q_orig, qs, qsf, grid, fs, out, st)
+               : launch_atoms_p<double>(p, gather, aa, q_orig, qs, qsf, grid, fs, out, st);
 }
 
 void destroy(md_spme *s) {
@@ -578,9 +616,11 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     SCK(salloc(&s->q, n));
     SCK(salloc(&s->qs, ns));
     SCK(salloc(&s->qsf, ns));
-    SCK(salloc(&s->grid, s->ngrid));
-    SCK(salloc(&s->ghat, s->nhalf));
-    SCK(salloc(&s->theta, s->nhalf));
+    s->f32 = c->params.precision == MD_MIXED;
+    const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
+    SCK(cudaMalloc(&s->grid, s->ngrid * rb));
+    SCK(cudaMalloc(&s->ghat, s->nhalf * 2 * rb));
+    SCK(cudaMalloc(&s->theta, s->nhalf * rb));
     SCK(salloc(&s->fs, 3 * ns));
     SCK(salloc(&s->part, s->nreal + s->nrecip));
     SCK(salloc(&s->dsum, 2));
@@ -597,16 +637,21 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     cudaError_t e = cudaMemcpyAsync(dbm, bm.data(), bm.size() * sizeof(double),
                                     cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) {
-        k_spme_theta<<<(int)((s->nhalf + 255) / 256), 256, 0, c->stream>>>(
-            s->theta, dbm, g, B.L[0], B.L[1], B.L[2], p->alpha, s->nhalf);
+        const int tb = (int)((s->nhalf + 255) / 256);
+        if (s->f32)
+            k_spme_theta<float><<<tb, 256, 0, c->stream>>>((float *)s->theta, dbm, g, B.L[0], B.L[1],
+                                                           B.L[2], p->alpha, s->nhalf);
+        else
+            k_spme_theta<double><<<tb, 256, 0, c->stream>>>((double *)s->theta, dbm, g, B.L[0],
+                                                            B.L[1], B.L[2], p->alpha, s->nhalf);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(dbm);
     if (e != cudaSuccess) return scuda(s, e, "influence table");
-    FCK(cufftPlan3d(&s->fwd, g.K[2], g.K[1], g.K[0], CUFFT_D2Z));
+    FCK(cufftPlan3d(&s->fwd, g.K[2], g.K[1], g.K[0], s->f32 ? CUFFT_R2C : CUFFT_D2Z));
     s->have_fwd = true;
-    FCK(cufftPlan3d(&s->bwd, g.K[2], g.K[1], g.K[0], CUFFT_Z2D));
+    FCK(cufftPlan3d(&s->bwd, g.K[2], g.K[1], g.K[0], s->f32 ? CUFFT_C2R : CUFFT_Z2D));
     s->have_bwd = true;
     FCK(cufftSetStream(s->fwd, c->stream));
     FCK(cufftSetStream(s->bwd, c->stream));
@@ -701,21 +746,36 @@ md_status md_spme_compute(md_spme *s, double *f, double *energy) {
     if (real_blocks > s->nreal) return sfail(s, MD_ERR_ARG, "internal: real-space partials");
 
     SCK(mark(0));
-    SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * sizeof(double), stream));
-    SCK(launch_atoms_p(s->p.order, false, aa, s->q, s->qs, s->qsf, s->grid, nullptr, nullptr, stream));
+    const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
+    SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * rb, stream));
+    SCK(launch_atoms_any(s->f32, s->p.order, false, aa, s->q, s->qs, s->qsf, s->grid, nullptr,
+                         nullptr, stream));
     SCK(mark(1));
     SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
               : launch_real<false>(c->T, ra, real_blocks, stream));
     SCK(mark(2));
-    FCK(cufftExecD2Z(s->fwd, s->grid, reinterpret_cast<cufftDoubleComplex *>(s->ghat)));
+    if (s->f32)
+        FCK(cufftExecR2C(s->fwd, (cufftReal *)s->grid, (cufftComplex *)s->ghat));
+    else
+        FCK(cufftExecD2Z(s->fwd, (cufftDoubleReal *)s->grid, (cufftDoubleComplex *)s->ghat));
     SCK(mark(3));
-    k_spme_influence<<<(int)s->nrecip, kThreads, 0, stream>>>(s->ghat, s->theta, s->nhalf, s->g.Kh,
-                                                             s->g.K[0], s->part + real_blocks);
+    if (s->f32)
+        k_spme_influence<float><<<(int)s->nrecip, kThreads, 0, stream>>>(
+            (float2 *)s->ghat, (const float *)s->theta, s->nhalf, s->g.Kh, s->g.K[0],
+            s->part + real_blocks);
+    else
+        k_spme_influence<double><<<(int)s->nrecip, kThreads, 0, stream>>>(
+            (double2 *)s->ghat, (const double *)s->theta, s->nhalf, s->g.Kh, s->g.K[0],
+            s->part + real_blocks);
     SCK(cudaGetLastError());
     SCK(mark(4));
-    FCK(cufftExecZ2D(s->bwd, reinterpret_cast<cufftDoubleComplex *>(s->ghat), s->grid));
+    if (s->f32)
+        FCK(cufftExecC2R(s->bwd, (cufftComplex *)s->ghat, (cufftReal *)s->grid));
+    else
+        FCK(cufftExecZ2D(s->bwd, (cufftDoubleComplex *)s->ghat, (cufftDoubleReal *)s->grid));
     SCK(mark(5));
-    SCK(launch_atoms_p(s->p.order, true, aa, nullptr, s->qs, nullptr, s->grid, s->fs, out, stream));
+    SCK(launch_atoms_any(s->f32, s->p.order, true, aa, nullptr, s->qs, nullptr, s->grid, s->fs, out,
+                         stream));
     SCK(mark(6));
     k_spme_sum<<<1, 1024, 0, stream>>>(s->part, real_blocks, s->nrecip, s->dsum);
     SCK(cudaGetLastError());
