@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-drift", action="store_true")
+    ap.add_argument("--no-spme", action="store_true")
+    ap.add_argument("--spme-workload", default="coulomb_fcc100_4m")
     return ap.parse_args()
 
 
@@ -170,6 +172,94 @@ BUILD_BYTES_PER_ATOM = 16.0 + 4.0
 # and the two parameter partials) and beyond rc (distance and test only).
 ADJ_FLOPS_IN, ADJ_FLOPS_OUT = 86, 11
 FP64_NOMINAL_TFLOPS = 1.25
+
+
+# Algorithmic bytes of the SPME kernels (R = grid real size: 4 mixed, 8 FP64).
+# Spread, per atom: r, packed cell, id, gathered charge (40 B) in, the slot's
+# charge in FP64 and FP32 (12 B) out; per grid point the zeroing write and one
+# read-modify-write (3 R).  Gather, per atom: r, cell, id, charge, real-space
+# force in (64 B), force out (24 B); per grid point one read (R).  Influence,
+# per half-spectrum element: Qhat read and written (4 R), theta read (R).
+# FFTs: the grid read and the half spectrum written, or back (R + 2 R per
+# element pair, counted on the grid and the half spectrum).  Real space:
+# 4 B per list entry, and per atom its shadow or FP64 position, charge and
+# count in, its force out.
+SPME_SPREAD_ATOM, SPME_GATHER_ATOM = 52.0, 88.0
+
+
+def spme_bytes(stage, n, n_list, ngrid, nhalf, rb, mixed):
+    if stage == "spread":
+        return SPME_SPREAD_ATOM * n + 3 * rb * ngrid
+    if stage == "gather":
+        return SPME_GATHER_ATOM * n + rb * ngrid
+    if stage == "influence":
+        return 5 * rb * nhalf
+    if stage in ("fft_forward", "fft_inverse"):
+        return rb * ngrid + 2 * rb * nhalf
+    per_atom = (16 + 4 + 4 + 24) if mixed else (24 + 8 + 4 + 24)
+    return 4.0 * n_list + per_atom * n
+
+
+def spme_leg(args, stream, hbm_peak):
+    """Long-range Coulomb by SPME (md_spme_compute) on a charged melt: the
+    LJ-melt positions with neutral random +-1 charges, alpha 1.25, real-space
+    cutoff 2.5, order-4 splines on a K^3 grid of ~0.44 sigma spacing.  Whole
+    calls timed with CUDA events (each call returns its energies to the host);
+    per-stage device times from md_spme_profile; the HBM view per stage."""
+    import numpy as np
+    import torch
+
+    import md_inputs as mi
+    from paper_2109_09056_b300 import SPME, MDSystem
+    from paper_2109_09056_b300 import api as A
+    cs = mi.charged_workload(args.spme_workload)
+    s = cs.lj
+    K = cs.K
+    ngrid = K[0] * K[1] * K[2]
+    nhalf = (K[0] // 2 + 1) * K[1] * K[2]
+    res = {"workload": args.spme_workload, "atoms": s.n, "alpha": cs.alpha, "rc": cs.rc,
+           "grid": list(K), "order": cs.order, "unit": "atoms/s (one md_spme_compute)"}
+    reps = max(args.steps // 3, 5)
+    for prec in ("mixed", "fp64"):
+        m = MDSystem(s.x, s.v, s.types, s.box, precision=prec, stream=stream)
+        sp = SPME(m, cs.q, alpha=cs.alpha, rc=cs.rc, K=K, order=cs.order)
+        dev = torch.device("cuda")
+        for _ in range(3):
+            sp.compute(device=dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            energies, _ = sp.compute(device=dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        sp.profile(True)
+        stages = []
+        for _ in range(3):
+            sp.compute(device=dev)
+            stages.append(sp.profile_read())
+        sp.profile(False)
+        stage_ms = {k: float(np.median([d[k] for d in stages])) for k in stages[0]}
+        nn = torch.empty(s.n, dtype=torch.int32, device=dev)      # row lengths only
+        pad = A.C.c_int32()
+        A.check(A.lib.md_get_neighbors(m.ctx.handle, A.C.c_void_p(nn.data_ptr()), None,
+                                       A.C.byref(pad)), m.ctx.handle)
+        n_list = int(nn.sum().item())
+        rb = 4 if prec == "mixed" else 8
+        hbm = {}
+        for k, t in stage_ms.items():
+            b = spme_bytes(k, s.n, n_list, ngrid, nhalf, rb, prec == "mixed")
+            hbm[k] = {"bytes": b, "achieved_gbs": b / (t * 1e-3) / 1e9,
+                      "frac": b / (t * 1e-3) / 1e9 / hbm_peak}
+        res[prec] = {"ms_per_call": ms, "value": s.n / (ms * 1e-3), "stage_ms": stage_ms,
+                     "hbm_view": hbm, "energy": energies}
+        sp.close()
+        m.close()
+    res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
+    res["hbm_peak_gbs"] = hbm_peak
+    return res
 
 
 def adjoint_leg(args, stream, dev):
@@ -550,6 +640,10 @@ def run_ours(args, dist):
     # ---- force-matching adjoint (FP64) ---------------------------------------
     if not args.no_adjoint:
         out["adjoint"] = adjoint_leg(args, stream, dev)
+
+    # ---- long-range Coulomb (SPME) ---------------------------------------------
+    if not args.no_spme:
+        out["spme"] = spme_leg(args, stream, hbm_peak)
 
     # ---- CPU baseline (oracle) on rank 0 at N = 1 ---------------------------
     cpu = None
