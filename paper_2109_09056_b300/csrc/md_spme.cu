@@ -404,6 +404,9 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                     sj[u] = __ldg(a.sh + j);
                     qj[u] = e[u] == kSelf ? 0.f : __ldg(a.qsf + j);
                 }
+                // the batch's terms are summed plainly, then added to the
+                // per-atom sums with one compensated add per component
+                float bx = 0.f, by = 0.f, bz = 0.f, be = 0.f;
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
                     const int cd = e[u] == kSelf ? 3 * (int)kCodeZero : 3 * (int)(e[u] >> MD_IDX_BITS);
@@ -415,14 +418,18 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                         const float qq = qi * qj[u];
                         const float rinv = rsqrtf(r2);
                         const float er = erfcf(a.alphaf * (r2 * rinv));
-                        const float ex = expf(-(a.alphaf * a.alphaf) * r2);
+                        const float ex = __expf(-(a.alphaf * a.alphaf) * r2);
                         const float g = qq * fmaf(er, rinv, a.c2af * ex) * (rinv * rinv);
-                        kahan_add(fx, cx, -g * dx);
-                        kahan_add(fy, cy, -g * dy);
-                        kahan_add(fz, cz, -g * dz);
-                        kahan_add(pe, cp, 0.5f * qq * er * rinv);
+                        bx = fmaf(-g, dx, bx);
+                        by = fmaf(-g, dy, by);
+                        bz = fmaf(-g, dz, bz);
+                        be = fmaf(0.5f * qq, er * rinv, be);
                     }
                 }
+                kahan_add(fx, cx, bx);
+                kahan_add(fy, cy, by);
+                kahan_add(fz, cz, bz);
+                kahan_add(pe, cp, be);
             }
             F[0] = (double)(fx - cx);
             F[1] = (double)(fy - cy);
@@ -616,6 +623,8 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     SCK(salloc(&s->q, n));
     SCK(salloc(&s->qs, ns));
     SCK(salloc(&s->qsf, ns));
+    SCK(cudaMemset(s->qs, 0, ns * sizeof(double)));   // padding slots stay uncharged
+    SCK(cudaMemset(s->qsf, 0, ns * sizeof(float)));
     s->f32 = c->params.precision == MD_MIXED;
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
     SCK(cudaMalloc(&s->grid, s->ngrid * rb));
