@@ -80,6 +80,20 @@ md_status md_spme_set_charges(md_spme *s, const double *q);
  * md_build_neighbors / CUDA / cuFFT. */
 md_status md_spme_compute(md_spme *s, double *f, double *energy);
 
+/* nsteps of velocity Verlet (paper, Introduction and Fig. 1: forces ->
+ * propagate -> resort) with the total force LJ + Coulomb: per step the
+ * context's kick and drift, its re-sort and list rebuild every rebuild_every
+ * steps, its LJ forces, the SPME forces added to them, and the closing
+ * half-kick.  The forces of the starting state are recomputed first.  energy:
+ * host array of 4 (may be NULL) for the final state: LJ PE, Coulomb energy
+ * (real + reciprocal + self + background), kinetic energy, total.  The
+ * context's own thermo records keep describing LJ only; after this call
+ * md_get_state's forces and md_step recompute LJ-only forces.  Synchronises the
+ * context's stream once per rebuild and at the end.  Errors: MD_ERR_ARG, and
+ * those of the context's sort, list build and forces (MD_ERR_NONFINITE,
+ * MD_ERR_NEIGH_OVERFLOW, MD_ERR_TIMEOUT, MD_ERR_CUDA). */
+md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy);
+
 /* Per-kernel device times of the last md_spme_compute, in ms, measured with
  * CUDA events on the context's stream when `on` was set by md_spme_profile:
  * ms[0] charge spread, [1] forward FFT, [2] influence (energy + multiply),

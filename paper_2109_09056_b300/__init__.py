@@ -13,7 +13,7 @@ from .api import (MDSystem, md_batch_create, md_bin_sort_noalloc, md_batch_therm
                   md_get_permutation, md_get_state, md_get_thermo, md_get_thermo_log, md_info,
                   md_debug_expire_waits, md_launch_count, md_params_default, md_profile, md_profile_read, md_profile_rebuild, md_set_params,
                   md_set_positions, md_set_state, md_step, SPME, md_spme_create, md_spme_set_charges,
-                  md_spme_compute, md_spme_profile, md_spme_profile_read, md_spme_destroy)
+                  md_spme_compute, md_spme_step, md_spme_profile, md_spme_profile_read, md_spme_destroy)
 from ._native import LIB_PATH, MD_FP64, MD_MIXED, MDError
 
 __all__ = [
@@ -22,7 +22,7 @@ __all__ = [
     "md_set_state", "md_launch_count", "md_debug_expire_waits", "md_bin_sort_noalloc", "md_set_params", "md_get_state", "md_get_permutation", "md_get_neighbors", "md_get_thermo",
     "md_get_thermo_log", "md_profile", "md_profile_read", "md_profile_rebuild", "md_destroy", "md_batch_create",
     "md_batch_thermo", "md_info", "md_params_default", "LJForce", "SPME", "md_spme_create",
-    "md_spme_set_charges", "md_spme_compute", "md_spme_profile", "md_spme_profile_read",
+    "md_spme_set_charges", "md_spme_compute", "md_spme_step", "md_spme_profile", "md_spme_profile_read",
     "md_spme_destroy",
 ]
 

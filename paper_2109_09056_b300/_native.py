@@ -100,6 +100,7 @@ SIGNATURES = {
     "md_spme_create": ([P, P, C.POINTER(md_spme_params), C.POINTER(P)], C.c_int),
     "md_spme_set_charges": ([P, P], C.c_int),
     "md_spme_compute": ([P, P, P], C.c_int),
+    "md_spme_step": ([P, C.c_int32, P], C.c_int),
     "md_spme_profile": ([P, C.c_int32], C.c_int),
     "md_spme_profile_read": ([P, P], C.c_int),
     "md_spme_last_error": ([P], C.c_char_p),

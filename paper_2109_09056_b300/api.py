@@ -424,6 +424,14 @@ def md_spme_compute(s: Spme, device=None, forces: bool = True) -> tuple:
     return {"real": e[0], "recip": e[1], "self": e[2], "total": e[3]}, f
 
 
+def md_spme_step(s: Spme, nsteps: int) -> dict:
+    """nsteps of Coulomb + LJ velocity Verlet; energies of the final state
+    {"pe_lj", "coulomb", "ke", "total"}."""
+    e = (C.c_double * 4)()
+    check_spme(lib.md_spme_step(s.handle, int(nsteps), e), s.handle)
+    return {"pe_lj": e[0], "coulomb": e[1], "ke": e[2], "total": e[3]}
+
+
 def md_spme_profile(s: Spme, on: bool = True) -> None:
     check_spme(lib.md_spme_profile(s.handle, int(bool(on))), s.handle)
 
@@ -456,6 +464,9 @@ class SPME:
 
     def compute(self, device=None, forces: bool = True) -> tuple:
         return md_spme_compute(self.solver, device, forces)
+
+    def step(self, nsteps: int) -> dict:
+        return md_spme_step(self.solver, nsteps)
 
     def profile(self, on: bool = True):
         md_spme_profile(self.solver, on)

@@ -512,6 +512,25 @@ md_status ensure_list(md_ctx *c) {
     return build_with_retry(c);
 }
 bool is_device_pointer(const void *p) { return is_device_ptr(p); }
+// Re-sort the drifted state into cells and rebuild the list (pad grown on
+// overflow), as md_step does at a rebuild step; c->step is the step of the state.
+md_status resort_and_build(md_ctx *c) {
+    md_status s = sort_build(c, false);
+    if (s) return s;
+    if (c->hflags->status & ST_TIMEOUT) return timeout_fail(c);
+    c->list_valid = true;
+    return MD_OK;
+}
+// Read the device flags and turn a frozen state into its status.
+md_status check_run_flags(md_ctx *c) {
+    md_status s = read_flags(c);
+    if (s) return s;
+    const uint32_t st = c->hflags->status;
+    if (st & ST_TIMEOUT) return timeout_fail(c);
+    if (st & ST_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position");
+    if (st & ST_OVERFLOW) return fail(c, MD_ERR_NEIGH_OVERFLOW, "a list row overflowed");
+    return MD_OK;
+}
 }  // namespace mdb
 
 md_status mdb::set_global_error(md_status s, const std::string &msg) {

@@ -29,6 +29,11 @@
 //   k_spme_gather   one thread per slot: spline gradients against dE/dQ, plus the
 //                   slot's real-space force, written in original atom order;
 // then one single-CTA sum of the energy partials (fixed order, deterministic).
+//
+// md_spme_step integrates Coulomb + LJ with velocity Verlet from the context's
+// non-fused launchers: kick + drift, re-sort and list at the rebuild cadence,
+// LJ forces (force-only mode), the SPME forces added to them in slot order,
+// then k_spme_half_kick closes the step.
 #include <cufft.h>
 
 #include <algorithm>
@@ -40,9 +45,11 @@
 #include "md_common.cuh"
 #include "md_spme.h"
 
-namespace mdb {
-md_status ensure_list(md_ctx *c);       // md_api.cu
-bool is_device_pointer(const void *p);  // md_api.cu
+namespace mdb {  // md_api.cu
+md_status ensure_list(md_ctx *c);
+bool is_device_pointer(const void *p);
+md_status resort_and_build(md_ctx *c);
+md_status check_run_flags(md_ctx *c);
 }  // namespace mdb
 
 using namespace mdb;
@@ -57,6 +64,7 @@ constexpr int kMaxGrid = 4096;
 constexpr int kRealBatch = 4;       // list entries per lane in flight (mixed real space)
 constexpr uint32_t kSelf = 0xFFFFFFFFu;  // batch slot past the row's end
 constexpr int kEvents = 7;
+enum { kSpread = 0, kGatherOut = 1, kGatherAcc = 2 };
 
 struct Geom {
     int32_t K[3];
@@ -82,8 +90,10 @@ struct md_spme {
     double *fs = nullptr;       // real-space forces per slot, SoA 3 x ns
     double *part = nullptr;     // energy partials: real [nreal], then recip [nrecip]
     int64_t nreal = 0, nrecip = 0;
-    double *dsum = nullptr;     // 2 doubles: E_real, E_recip
-    double *hsum = nullptr;     // pinned mirror
+    double *dsum = nullptr;     // 4 doubles: E_real, E_recip, KE (md_spme_step), spare
+    double *hsum = nullptr;     // pinned mirror of dsum, then the LJ PE
+    double *hpe = nullptr;      // = hsum + 4
+    double *kpart = nullptr;    // kinetic-energy partials of the half-kick
     double *fstage = nullptr;   // n x 3 device output when the caller's f is host memory
     double e_const = 0.0;       // E_self + E_bg
     cufftHandle fwd = 0, bwd = 0;
@@ -168,6 +178,28 @@ __device__ __forceinline__ double grid_stencil(double x, double kl, double Kd, i
 
 // ---- kernels ------------------------------------------------------------------
 
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic CTA sum of one double per thread into out (thread 0 writes).
+template <int NT>
+__device__ __forceinline__ void cta_sum_to(double v, double *out) {
+    __shared__ double red[NT / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+
 struct AtomArgs {
     const Box *box;
     const double *ctab;
@@ -216,8 +248,10 @@ __global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const doub
 }
 
 // Forces on the atoms: F = -q (K/L) sum over the P^3 stencil of the spline
-// gradient times dE/dQ, plus the slot's real-space force; out in original order.
-template <int P, typename R>
+// gradient times dE/dQ, plus the slot's real-space force; written to `out` in
+// original order (n x 3), or with ACC added to the context's slot-order force
+// array (SoA, 3 x ns).
+template <int P, typename R, bool ACC>
 __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const double *__restrict__ qs,
                                                           const R *__restrict__ dEdQ,
                                                           const double *__restrict__ fs,
@@ -262,30 +296,41 @@ __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const doub
         fr[1] = -q * a.g.kl[1] * (double)gy;
         fr[2] = -q * a.g.kl[2] * (double)gz;
     }
-    const int64_t g = a.id[i];
+    if (ACC) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) out[3 * g + d] = fs[d * a.ns + i] + fr[d];
-}
-
-template <typename V>
-__device__ __forceinline__ V warp_sum(V v) {
+        for (int d = 0; d < 3; ++d) out[d * a.ns + i] += fs[d * a.ns + i] + fr[d];
+    } else {
+        const int64_t g = a.id[i];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Deterministic CTA sum of one double per thread into out (thread 0 writes).
-template <int NT>
-__device__ __forceinline__ void cta_sum_to(double v, double *out) {
-    __shared__ double red[NT / 32];
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
-        t = warp_sum(t);
-        if (threadIdx.x == 0) *out = t;
+        for (int d = 0; d < 3; ++d) out[3 * g + d] = fs[d * a.ns + i] + fr[d];
     }
+}
+
+// Closing half-kick of velocity Verlet, v += dt/2 F/m (kick = 1), and the
+// kinetic energy of the resulting velocities summed per CTA (fixed order).
+__global__ void __launch_bounds__(kThreads) k_spme_half_kick(const Box *__restrict__ box,
+                                                             const Pair *__restrict__ pair,
+                                                             int64_t ns, int kick,
+                                                             const int32_t *__restrict__ type,
+                                                             const double *__restrict__ f,
+                                                             double *__restrict__ v,
+                                                             double *__restrict__ part) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (i < box[0].n) {
+        const int ty = type[i];
+        const double hdtm = pair->hdtm[ty], m = pair->mass[ty];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double vv = v[d * ns + i];
+            if (kick) {
+                vv = fma(hdtm, f[d * ns + i], vv);
+                v[d * ns + i] = vv;
+            }
+            ke += 0.5 * m * vv * vv;
+        }
+    }
+    cta_sum_to<kThreads>(ke, part + blockIdx.x);
 }
 
 template <typename R> struct Cplx;
@@ -533,38 +578,40 @@ cudaError_t launch_real(int T, const RealArgs &ra, int blocks, cudaStream_t st) 
 }
 
 template <int P, typename R>
-cudaError_t launch_atoms(bool gather, const AtomArgs &aa, const double *q_orig, double *qs,
+cudaError_t launch_atoms(int mode, const AtomArgs &aa, const double *q_orig, double *qs,
                          float *qsf, void *grid, const double *fs, double *out, cudaStream_t st) {
     const int blocks = (int)((aa.ns + kThreads - 1) / kThreads);
-    if (gather)
-        k_spme_gather<P, R><<<blocks, kThreads, 0, st>>>(aa, qs, (const R *)grid, fs, out);
+    if (mode == kGatherOut)
+        k_spme_gather<P, R, false><<<blocks, kThreads, 0, st>>>(aa, qs, (const R *)grid, fs, out);
+    else if (mode == kGatherAcc)
+        k_spme_gather<P, R, true><<<blocks, kThreads, 0, st>>>(aa, qs, (const R *)grid, fs, out);
     else
         k_spme_spread<P, R><<<blocks, kThreads, 0, st>>>(aa, q_orig, qs, qsf, (R *)grid);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_atoms_p(int p, bool gather, const AtomArgs &aa, const double *q_orig, double *qs,
+cudaError_t launch_atoms_p(int p, int mode, const AtomArgs &aa, const double *q_orig, double *qs,
                            float *qsf, void *grid, const double *fs, double *out, cudaStream_t st) {
     switch (p) {
-        case 4: return launch_atoms<4, R>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
-        case 6: return launch_atoms<6, R>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
-        case 8: return launch_atoms<8, R>(gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 4: return launch_atoms<4, R>(mode, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 6: return launch_atoms<6, R>(mode, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 8: return launch_atoms<8, R>(mode, aa, q_orig, qs, qsf, grid, fs, out, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_atoms_any(bool f32, int p, bool gather, const AtomArgs &aa, const double *q_orig,
+cudaError_t launch_atoms_any(bool f32, int p, int mode, const AtomArgs &aa, const double *q_orig,
                              double *qs, float *qsf, void *grid, const double *fs, double *out,
                              cudaStream_t st) {
-    return f32 ? launch_atoms_p<float>(p, gather, aa, q_orig, qs, qsf, grid, fs, out, st)
-               : launch_atoms_p<double>(p, gather, aa, q_orig, qs, qsf, grid, fs, out, st);
+    return f32 ? launch_atoms_p<float>(p, mode, aa, q_orig, qs, qsf, grid, fs, out, st)
+               : launch_atoms_p<double>(p, mode, aa, q_orig, qs, qsf, grid, fs, out, st);
 }
 
 void destroy(md_spme *s) {
     auto F = [](void *p) { if (p) cudaFree(p); };
     F(s->q); F(s->qs); F(s->qsf); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part);
-    F(s->dsum); F(s->fstage);
+    F(s->dsum); F(s->fstage); F(s->kpart);
     if (s->hsum) cudaFreeHost(s->hsum);
     if (s->have_fwd) cufftDestroy(s->fwd);
     if (s->have_bwd) cufftDestroy(s->bwd);
@@ -632,8 +679,9 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     SCK(cudaMalloc(&s->theta, s->nhalf * rb));
     SCK(salloc(&s->fs, 3 * ns));
     SCK(salloc(&s->part, s->nreal + s->nrecip));
-    SCK(salloc(&s->dsum, 2));
-    SCK(cudaMallocHost(reinterpret_cast<void **>(&s->hsum), 2 * sizeof(double)));
+    SCK(salloc(&s->dsum, 4));
+    SCK(cudaMallocHost(reinterpret_cast<void **>(&s->hsum), 5 * sizeof(double)));
+    s->hpe = s->hsum + 4;
     for (auto &e : s->ev) SCK(cudaEventCreate(&e));
     // influence table, built once
     std::vector<double> bm(g.K[0] + g.K[1] + g.K[2]);
@@ -704,21 +752,17 @@ md_status md_spme_set_charges(md_spme *s, const double *q) {
     return load_charges(s, q);
 }
 
-md_status md_spme_compute(md_spme *s, double *f, double *energy) {
-    if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
+}  // extern "C"
+
+namespace {
+
+// Enqueues one SPME evaluation at the context's current positions on its
+// stream: forces to `out` (original order, n x 3) or, with acc, added to the
+// context's slot-order forces; E_real and E_recip to s->dsum.  No host sync.
+md_status enqueue(md_spme *s, double *out, bool acc) {
     md_ctx *c = s->ctx;
-    md_status st = ensure_list(c);
-    if (st != MD_OK) return sfail(s, st, c->err);
     const bool mixed = c->params.precision == MD_MIXED;
     cudaStream_t stream = c->stream;
-    const int64_t n = c->n_total;
-    double *out = nullptr;
-    if (f && is_device_pointer(f)) {
-        out = f;
-    } else {
-        if (!s->fstage) SCK(salloc(&s->fstage, 3 * n));
-        out = s->fstage;
-    }
     auto mark = [&](int k) -> cudaError_t {
         return s->prof ? cudaEventRecord(s->ev[k], stream) : cudaSuccess;
     };
@@ -757,7 +801,7 @@ md_status md_spme_compute(md_spme *s, double *f, double *energy) {
     SCK(mark(0));
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
     SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * rb, stream));
-    SCK(launch_atoms_any(s->f32, s->p.order, false, aa, s->q, s->qs, s->qsf, s->grid, nullptr,
+    SCK(launch_atoms_any(s->f32, s->p.order, kSpread, aa, s->q, s->qs, s->qsf, s->grid, nullptr,
                          nullptr, stream));
     SCK(mark(1));
     SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
@@ -783,29 +827,123 @@ md_status md_spme_compute(md_spme *s, double *f, double *energy) {
     else
         FCK(cufftExecZ2D(s->bwd, (cufftDoubleComplex *)s->ghat, (cufftDoubleReal *)s->grid));
     SCK(mark(5));
-    SCK(launch_atoms_any(s->f32, s->p.order, true, aa, nullptr, s->qs, nullptr, s->grid, s->fs, out,
-                         stream));
+    SCK(launch_atoms_any(s->f32, s->p.order, acc ? kGatherAcc : kGatherOut, aa, nullptr, s->qs,
+                         nullptr, s->grid, s->fs, out, stream));
     SCK(mark(6));
     k_spme_sum<<<1, 1024, 0, stream>>>(s->part, real_blocks, s->nrecip, s->dsum);
     SCK(cudaGetLastError());
+    return MD_OK;
+}
+
+md_status read_profile(md_spme *s) {
+    if (!s->prof) return MD_OK;
+    // event k -> k+1 brackets: spread, real, fwd FFT, influence, inv FFT, gather
+    static const int slot[6] = {0, 5, 1, 2, 3, 4};
+    for (int k = 0; k < 6; ++k) {
+        float ms = 0.f;
+        SCK(cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]));
+        s->ms[slot[k]] = ms;
+    }
+    return MD_OK;
+}
+
+// LJ forces (force-only mode) at the context's current positions, then the
+// SPME forces added to them: the total force of a Coulomb + LJ state.
+md_status total_forces(md_spme *s) {
+    md_ctx *c = s->ctx;
+    SCK(launch_force(c, MODE_FORCE_ONLY));
+    return enqueue(s, c->f, true);
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_spme_compute(md_spme *s, double *f, double *energy) {
+    if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
+    md_ctx *c = s->ctx;
+    md_status st = ensure_list(c);
+    if (st != MD_OK) return sfail(s, st, c->err);
+    const int64_t n = c->n_total;
+    double *out = nullptr;
+    if (f && is_device_pointer(f)) {
+        out = f;
+    } else {
+        if (!s->fstage) SCK(salloc(&s->fstage, 3 * n));
+        out = s->fstage;
+    }
+    st = enqueue(s, out, false);
+    if (st != MD_OK) return st;
+    cudaStream_t stream = c->stream;
     SCK(cudaMemcpyAsync(s->hsum, s->dsum, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
     if (f && out != f)
         SCK(cudaMemcpyAsync(f, out, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     SCK(cudaStreamSynchronize(stream));
-    if (s->prof) {
-        // event k -> k+1 brackets: spread, real, fwd FFT, influence, inv FFT, gather
-        static const int slot[6] = {0, 5, 1, 2, 3, 4};
-        for (int k = 0; k < 6; ++k) {
-            float ms = 0.f;
-            SCK(cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]));
-            s->ms[slot[k]] = ms;
-        }
-    }
+    st = read_profile(s);
+    if (st != MD_OK) return st;
     if (energy) {
         energy[0] = s->hsum[0];
         energy[1] = s->hsum[1];
         energy[2] = s->e_const;
         energy[3] = (s->hsum[0] + s->hsum[1]) + s->e_const;
+    }
+    return MD_OK;
+}
+
+md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
+    if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
+    if (nsteps < 0) return sfail(s, MD_ERR_ARG, "nsteps must be >= 0");
+    md_ctx *c = s->ctx;
+    md_status st = ensure_list(c);
+    if (st != MD_OK) return sfail(s, st, c->err);
+    cudaStream_t stream = c->stream;
+    const int every = c->params.rebuild_every;
+    const bool prof = s->prof;
+    s->prof = false;
+    // the opening half-kick needs the total force of the current state
+    st = total_forces(s);
+    if (st != MD_OK) return st;
+    c->forces_valid = false;   // c->f holds LJ + Coulomb, not what md_step expects
+    const int kb = (int)((c->ns + kThreads - 1) / kThreads);
+    if (!s->kpart) SCK(salloc(&s->kpart, kb));
+    for (int32_t k = 0; k < nsteps; ++k) {
+        SCK(launch_kick_drift(c));
+        c->ready = false;
+        const int64_t n = c->step + 1;
+        c->step = n;
+        if (n % every == 0) {
+            st = resort_and_build(c);
+            if (st != MD_OK) return sfail(s, st, c->err);
+            c->sorted_at = n;
+            c->built_at = n;
+        }
+        st = total_forces(s);
+        if (st != MD_OK) return st;
+        k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 1, c->type[c->oc],
+                                                       c->f, c->v[c->oc], s->kpart);
+        SCK(cudaGetLastError());
+        c->ready = true;
+    }
+    s->prof = prof;
+    // energies of the final state: LJ PE from the last force launch's partials,
+    // Coulomb from the last SPME sums, KE from the last half-kick (or the
+    // current velocities when no step ran)
+    SCK(launch_finalize(c, MODE_FORCE_ONLY));
+    if (nsteps == 0)
+        k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 0, c->type[c->oc],
+                                                       c->f, c->v[c->oc], s->kpart);
+    k_spme_sum<<<1, 1024, 0, stream>>>(s->kpart, kb, 0, s->dsum + 2);
+    SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(s->hsum, s->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaMemcpyAsync(s->hpe, c->tbox, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    st = check_run_flags(c);
+    if (st != MD_OK) return sfail(s, st, c->err);
+    if (energy) {
+        const double ecoul = (s->hsum[0] + s->hsum[1]) + s->e_const;
+        energy[0] = *s->hpe;
+        energy[1] = ecoul;
+        energy[2] = s->hsum[2];
+        energy[3] = (energy[0] + energy[1]) + energy[2];
     }
     return MD_OK;
 }

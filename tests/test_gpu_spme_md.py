@@ -1,0 +1,148 @@
+"""Coulomb + LJ dynamics (md_spme_step) against a velocity-Verlet loop over
+the oracles' forces (C LJ oracle + numpy Ewald/SPME oracle), through the C
+ABI, on a B300; and energy conservation of the combined dynamics.
+
+Trajectory: 864 atoms (6^3 FCC melt cells, jitter 0.1), neutral random +-1
+charges, alpha 1.25, rc 2.5, 24^3 grid, order 4, dt 0.005, 30 steps with a
+re-sort and list rebuild every 4 steps.  The oracle takes every pair by brute
+force at every step; the GPU takes them from its Verlet list, which holds every
+pair within rc only while no atom has moved more than skin/2 since the build,
+so the cadence is kept short enough for that to hold throughout (the Coulomb
+forces accelerate atoms beyond what a 20-step cadence allows at this
+temperature).  Positions (modulo the box) and velocities must match the
+oracle's to 1e-9 (FP64) / 1e-5 (mixed) relative, and the final energies to the
+same bars.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import md_inputs as mi
+import oracle
+from oracle import ewald as ew
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_util import make, rel_l2  # noqa: E402
+from paper_2109_09056_b300 import SPME  # noqa: E402
+
+ALPHA, RC, K, ORDER = 1.25, 2.5, (24, 24, 24), 4
+
+
+def small_charged():
+    s = mi.lj_melt(6, seed=3, jitter=0.1)
+    s.rebuild_every = 4
+    q = mi.neutral_charges(s.n, np.random.default_rng(17))
+    return s, q
+
+
+def oracle_forces(x, q, s):
+    xw = oracle.wrap(x, s.box)[0]
+    f_lj, _, pe = oracle.lj_forces(xw, s.types, s.box)
+    ek, fk = ew.spme_reciprocal(xw, q, s.box, ALPHA, K, ORDER)
+    er, fr = ew.ewald_real(xw, q, s.box, ALPHA, RC)
+    ec = ek + er + ew.ewald_self(q, ALPHA) + ew.ewald_background(q, s.box, ALPHA)
+    return f_lj + fk + fr, pe, ec
+
+
+def oracle_verlet(s, q, nsteps):
+    """Velocity Verlet (m = 1): v += dt/2 F; x += dt v; F = F(x); v += dt/2 F."""
+    x, v = s.x.copy(), s.v.copy()
+    f, pe, ec = oracle_forces(x, q, s)
+    for _ in range(nsteps):
+        v = v + 0.5 * s.dt * f
+        x = x + s.dt * v
+        f, pe, ec = oracle_forces(x, q, s)
+        v = v + 0.5 * s.dt * f
+    return x, v, pe, ec, 0.5 * float((v * v).sum())
+
+
+def periodic_diff(a, b, box):
+    d = a - b
+    return d - box * np.round(d / box)
+
+
+@pytest.fixture(scope="module")
+def reference():
+    s, q = small_charged()
+    return s, q, oracle_verlet(s, q, 30)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_step_trajectory_matches_oracle(reference, precision):
+    s, q, (x_o, v_o, pe_o, ec_o, ke_o) = reference
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    sysm = make(s, precision)
+    sp = SPME(sysm, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    e = sp.step(30)
+    st = sysm.state(forces=False)
+    dx = periodic_diff(st["x"], x_o, s.box)
+    assert np.linalg.norm(dx) <= tol * np.linalg.norm(x_o)
+    assert rel_l2(st["v"], v_o) <= tol
+    assert abs(e["pe_lj"] - pe_o) <= tol * abs(pe_o)
+    assert abs(e["coulomb"] - ec_o) <= tol * abs(ec_o)
+    assert abs(e["ke"] - ke_o) <= tol * abs(ke_o)
+    assert e["total"] == pytest.approx(e["pe_lj"] + e["coulomb"] + e["ke"], rel=1e-14)
+    # zero steps: the energies of the current state, state unchanged
+    e0 = sp.step(0)
+    assert e0["ke"] == pytest.approx(e["ke"], rel=1e-12)
+    st0 = sysm.state(forces=False)
+    assert np.array_equal(st0["x"], st["x"])
+    sp.close()
+    sysm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_step_chunks_equal_one_run(precision):
+    """Two calls of 15 steps give the state of one call of 30 (the forces of
+    the starting state are recomputed at each call)."""
+    s, q = small_charged()
+    a = make(s, precision)
+    b = make(s, precision)
+    sa = SPME(a, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    sb = SPME(b, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    ea = sa.step(30)
+    sb.step(15)
+    eb = sb.step(15)
+    xa, xb = a.state(forces=False)["x"], b.state(forces=False)["x"]
+    tol = 1e-11 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(periodic_diff(xa, xb, s.box)) <= tol * np.linalg.norm(xa)
+    assert eb["total"] == pytest.approx(ea["total"], rel=tol)
+    for o in (sa, sb):
+        o.close()
+    a.close()
+    b.close()
+
+
+def test_spme_step_energy_conservation():
+    """NVE with the shifted LJ potential (energy continuous at rc) and SPME
+    Coulomb on the 4,000-atom charged melt over 2 time units, both
+    precisions: no dangerous build (list rebuilt every 0.02 time units), the
+    total energy's largest deviation falls with dt^2 (ratio 2.5-6 for dt
+    halved) and stays below 1e-4 per atom at dt = 0.002, and the two
+    precisions agree to 1e-6 per atom."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    dev = {}
+    for prec in ("fp64", "mixed"):
+        for dt, every in ((0.004, 5), (0.002, 10)):
+            m = make(dataclasses.replace(s, dt=dt, rebuild_every=every), prec,
+                     shift_energy=True, check_displacement=True)
+            sp = SPME(m, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+            chunk = int(round(0.1 / dt))
+            E = [sp.step(0)["total"]] + [sp.step(chunk)["total"] for _ in range(20)]
+            assert m.thermo()["dangerous_builds"] == 0
+            dev[prec, dt] = np.abs(np.array(E) - E[0]).max() / s.n
+            dev[prec, dt, "E"] = np.array(E) / s.n
+            sp.close()
+            m.close()
+    for prec in ("fp64", "mixed"):
+        ratio = dev[prec, 0.004] / dev[prec, 0.002]
+        assert 2.5 <= ratio <= 6.0, (prec, ratio)
+        assert dev[prec, 0.002] <= 1e-4
+    assert np.abs(dev["fp64", 0.002, "E"] - dev["mixed", 0.002, "E"]).max() <= 1e-6
