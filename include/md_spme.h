@@ -25,7 +25,9 @@
  * gradient of Q contracted with dE/dQ = inverse FFT of theta FFT(Q).
  *
  * Conventions are those of md.h (status returns, host-or-device pointers,
- * original atom order, the context's stream).  Arithmetic follows the
+ * original atom order, the context's stream; the real-space pass runs on a
+ * solver-owned side stream, ordered after the context's stream and before the
+ * work that needs it by events, unless profiling is on).  Arithmetic follows the
  * context's precision.  MD_FP64: everything in FP64 (double-complex FFTs).
  * MD_MIXED: reciprocal part with FP32 spline weights, an FP32 grid,
  * single-precision FFTs and an FP32 gather; real-space pairs in FP32 on the

@@ -13,9 +13,9 @@
 // a 384^3 double-precision FFT pair alone took 15 ms there, against the
 // memory-bound few tenths of a millisecond of the FP32 pair.
 //
-// One md_spme_compute is six launches on the context's stream:
-//   k_spme_spread   one thread per slot: charge of the slot's atom (gathered by
-//                   its original id), scaled fractional coordinates from the
+// One md_spme_compute is these launches on the context's stream:
+//   k_spme_charges  charge of each slot's atom, gathered by its original id;
+//   k_spme_spread   one thread per slot: scaled fractional coordinates from the
 //                   FP64 cell-relative position, order-p spline weights by their
 //                   recursion, p^3 atomic adds into the grid Q;
 //   k_spme_real     the real-space erfc pairs over the context's Verlet list
@@ -29,6 +29,10 @@
 //   k_spme_gather   one thread per slot: spline gradients against dE/dQ, plus the
 //                   slot's real-space force, written in original atom order;
 // then one single-CTA sum of the energy partials (fixed order, deterministic).
+// The real-space pass depends only on the charges: it runs on a side stream,
+// forked after k_spme_charges and joined before the gather, beside the
+// reciprocal chain (it is issue-bound, the chain atomic- and memory-bound).
+// With profiling on, the launches run in order on one stream instead.
 //
 // md_spme_step integrates Coulomb + LJ with velocity Verlet from the context's
 // non-fused launchers: kick + drift, re-sort and list at the rebuild cadence,
@@ -62,6 +66,10 @@ constexpr int kThreads = 256;       // spread / gather / influence CTAs
 constexpr int kRealBlock = 256;     // real-space CTA (8 warps)
 constexpr int kMaxGrid = 4096;
 constexpr int kRealBatch = 4;       // list entries per lane in flight (mixed real space)
+#ifndef MD_SPME_REAL_CTAS
+#define MD_SPME_REAL_CTAS 4   // the real-space kernel's register-limited residency
+#endif
+constexpr int kRealCtasPerSm = MD_SPME_REAL_CTAS;  // persistent mixed real-space grid
 constexpr uint32_t kSelf = 0xFFFFFFFFu;  // batch slot past the row's end
 constexpr int kEvents = 7;
 enum { kSpread = 0, kGatherOut = 1, kGatherAcc = 2 };
@@ -100,6 +108,8 @@ struct md_spme {
     bool have_fwd = false, have_bwd = false;
     bool prof = false;
     cudaEvent_t ev[kEvents] = {};
+    cudaStream_t side = nullptr;        // real-space pass beside the reciprocal chain
+    cudaEvent_t fork = nullptr, join = nullptr;
     double ms[6] = {0, 0, 0, 0, 0, 0};
     std::string err;
 };
@@ -210,17 +220,27 @@ struct AtomArgs {
     Geom g;
 };
 
+// Charge of each slot's atom (gathered by its original id), FP64 and FP32.
+__global__ void __launch_bounds__(kThreads) k_spme_charges(const Box *__restrict__ box, int64_t ns,
+                                                           const int32_t *__restrict__ id,
+                                                           const double *__restrict__ q_orig,
+                                                           double *__restrict__ qs,
+                                                           float *__restrict__ qsf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns || i >= box[0].n) return;
+    const double q = q_orig[id[i]];
+    qs[i] = q;
+    qsf[i] = (float)q;
+}
+
 template <int P, typename R>
-__global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const double *__restrict__ q_orig,
-                                                          double *__restrict__ qs,
-                                                          float *__restrict__ qsf,
+__global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const double *__restrict__ qs,
                                                           R *__restrict__ grid) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.ns) return;
     const Box &B = a.box[0];
-    const double q = i < B.n ? q_orig[a.id[i]] : 0.0;
-    qs[i] = q;
-    qsf[i] = (float)q;
+    if (i >= B.n) return;
+    const double q = qs[i];
     if (q == 0.0) return;
     int cc[3];
     unpack_cell(a.cellc[i], cc[0], cc[1], cc[2]);
@@ -421,9 +441,9 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane % T;
-    const int64_t wt = (int64_t)blockIdx.x * (kRealBlock / 32) + (threadIdx.x >> 5);
     double pe_lane = 0.0;
-    if (wt < a.nwt) {
+    for (int64_t wt = (int64_t)blockIdx.x * (kRealBlock / 32) + (threadIdx.x >> 5); wt < a.nwt;
+         wt += (int64_t)gridDim.x * (kRealBlock / 32)) {
         const int64_t i = wt * A + lane / T;
         const bool valid = i < B.n;
         const int ni = valid ? min(a.nn[i], a.pad) : 0;
@@ -479,7 +499,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
             F[0] = (double)(fx - cx);
             F[1] = (double)(fy - cy);
             F[2] = (double)(fz - cz);
-            pe_lane = (double)(pe - cp);
+            pe_lane += (double)(pe - cp);
         } else {
             const double rix = a.r[i], riy = a.r[a.ns + i], riz = a.r[2 * a.ns + i];
             const double qi = a.qs[i];
@@ -507,7 +527,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
             F[0] = fx;
             F[1] = fy;
             F[2] = fz;
-            pe_lane = pe;
+            pe_lane += pe;
         }
 #pragma unroll
         for (int o = T / 2; o; o >>= 1) {
@@ -586,7 +606,7 @@ cudaError_t launch_atoms(int mode, const AtomArgs &aa, const double *q_orig, dou
     else if (mode == kGatherAcc)
         k_spme_gather<P, R, true><<<blocks, kThreads, 0, st>>>(aa, qs, (const R *)grid, fs, out);
     else
-        k_spme_spread<P, R><<<blocks, kThreads, 0, st>>>(aa, q_orig, qs, qsf, (R *)grid);
+        k_spme_spread<P, R><<<blocks, kThreads, 0, st>>>(aa, qs, (R *)grid);
     return cudaGetLastError();
 }
 
@@ -617,6 +637,9 @@ void destroy(md_spme *s) {
     if (s->have_bwd) cufftDestroy(s->bwd);
     for (auto e : s->ev)
         if (e) cudaEventDestroy(e);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
+    if (s->side) cudaStreamDestroy(s->side);
 }
 
 md_status load_charges(md_spme *s, const double *q) {
@@ -683,6 +706,9 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     SCK(cudaMallocHost(reinterpret_cast<void **>(&s->hsum), 5 * sizeof(double)));
     s->hpe = s->hsum + 4;
     for (auto &e : s->ev) SCK(cudaEventCreate(&e));
+    SCK(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
+    SCK(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
+    SCK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     // influence table, built once
     std::vector<double> bm(g.K[0] + g.K[1] + g.K[2]);
     if (!spline_moduli(p->order, g.K[0], bm.data()) ||
@@ -795,17 +821,35 @@ md_status enqueue(md_spme *s, double *out, bool acc) {
     ra.alphaf = (float)ra.alpha;
     ra.rc2f = (float)ra.rc2;
     ra.c2af = (float)ra.c2a;
-    const int real_blocks = (int)((ra.nwt + kRealBlock / 32 - 1) / (kRealBlock / 32));
+    // beside the reciprocal chain the mixed real-space pass takes a persistent
+    // grid of kRealCtasPerSm CTAs per SM (grid-stride over warp tiles), leaving
+    // room on every SM for the chain's kernels; the FP64 pass (which dominates
+    // its call) and a profiled pass take one warp per tile
+    const bool overlap = !s->prof;
+    const int64_t tiles_blocks = (ra.nwt + kRealBlock / 32 - 1) / (kRealBlock / 32);
+    const int real_blocks = (int)std::min<int64_t>(
+        tiles_blocks, overlap && mixed ? (int64_t)kRealCtasPerSm * c->nsm : tiles_blocks);
     if (real_blocks > s->nreal) return sfail(s, MD_ERR_ARG, "internal: real-space partials");
 
     SCK(mark(0));
+    k_spme_charges<<<(int)((c->ns + kThreads - 1) / kThreads), kThreads, 0, stream>>>(
+        c->dbox, c->ns, c->id[c->oc], s->q, s->qs, s->qsf);
+    SCK(cudaGetLastError());
+    if (overlap) {
+        SCK(cudaEventRecord(s->fork, stream));
+        SCK(cudaStreamWaitEvent(s->side, s->fork, 0));
+        SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, s->side)
+                  : launch_real<false>(c->T, ra, real_blocks, s->side));
+        SCK(cudaEventRecord(s->join, s->side));
+    }
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
     SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * rb, stream));
     SCK(launch_atoms_any(s->f32, s->p.order, kSpread, aa, s->q, s->qs, s->qsf, s->grid, nullptr,
                          nullptr, stream));
     SCK(mark(1));
-    SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
-              : launch_real<false>(c->T, ra, real_blocks, stream));
+    if (!overlap)
+        SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
+                  : launch_real<false>(c->T, ra, real_blocks, stream));
     SCK(mark(2));
     if (s->f32)
         FCK(cufftExecR2C(s->fwd, (cufftReal *)s->grid, (cufftComplex *)s->ghat));
@@ -827,6 +871,7 @@ md_status enqueue(md_spme *s, double *out, bool acc) {
     else
         FCK(cufftExecZ2D(s->bwd, (cufftDoubleComplex *)s->ghat, (cufftDoubleReal *)s->grid));
     SCK(mark(5));
+    if (overlap) SCK(cudaStreamWaitEvent(stream, s->join, 0));
     SCK(launch_atoms_any(s->f32, s->p.order, acc ? kGatherAcc : kGatherOut, aa, nullptr, s->qs,
                          nullptr, s->grid, s->fs, out, stream));
     SCK(mark(6));
@@ -967,6 +1012,7 @@ const char *md_spme_last_error(const md_spme *s) {
 void md_spme_destroy(md_spme *s) {
     if (!s) return;
     if (s->ctx && s->ctx->stream) cudaStreamSynchronize(s->ctx->stream);
+    if (s->side) cudaStreamSynchronize(s->side);
     destroy(s);
     delete s;
 }
