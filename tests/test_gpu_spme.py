@@ -170,3 +170,19 @@ def test_spme_fullsize_sampled(precision):
     assert rel_l2(f[idx], Fr + Fk) <= tol(precision)
     sp.close()
     sysm.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_lanes_per_atom(precision, lanes):
+    """The real-space pass walks the context's list layout: every lanes-per-atom
+    layout (1, 2, 8 besides the default 4) gives the oracle's forces."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, precision, lanes_per_atom=lanes)
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, precision)
+    sysm.step(21)                          # a rebuild in between
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, precision)
+    sp.close()
+    sysm.close()
