@@ -220,6 +220,39 @@ struct AtomArgs {
     Geom g;
 };
 
+// Adds v[0..P-1] to the P consecutive floats at p with vector atomics: H
+// leading elements bring p to a 16-byte boundary (H = 0..3, from p's
+// alignment), then float4 adds, then a float2 and/or a float for the rest.
+template <int P, int H>
+__device__ __forceinline__ void red_run_h(float *p, const float (&v)[P]) {
+    static_assert(H >= 0 && H <= 3, "head");
+    if (H == 1) atomicAdd(p, v[0]);
+    if (H == 2) atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+    if (H == 3) {
+        atomicAdd(p, v[0]);
+        atomicAdd(reinterpret_cast<float2 *>(p + 1), make_float2(v[1], v[2]));
+    }
+    constexpr int h = H < P ? H : P;
+    constexpr int rest = P - h;
+#pragma unroll
+    for (int k = 0; k < rest / 4; ++k)
+        atomicAdd(reinterpret_cast<float4 *>(p + h + 4 * k),
+                  make_float4(v[h + 4 * k], v[h + 4 * k + 1], v[h + 4 * k + 2], v[h + 4 * k + 3]));
+    constexpr int t = h + 4 * (rest / 4);
+    if ((rest % 4) >= 2) atomicAdd(reinterpret_cast<float2 *>(p + t), make_float2(v[t], v[t + 1]));
+    if ((rest % 4) & 1) atomicAdd(p + P - 1, v[P - 1]);
+}
+
+template <int P>
+__device__ __forceinline__ void red_run(float *p, const float (&v)[P]) {
+    switch ((reinterpret_cast<uintptr_t>(p) >> 2) & 3) {
+        case 0: red_run_h<P, 0>(p, v); break;
+        case 1: red_run_h<P, 3>(p, v); break;
+        case 2: red_run_h<P, 2>(p, v); break;
+        default: red_run_h<P, 1>(p, v); break;
+    }
+}
+
 // Charge of each slot's atom (gathered by its original id), FP64 and FP32.
 __global__ void __launch_bounds__(kThreads) k_spme_charges(const Box *__restrict__ box, int64_t ns,
                                                            const int32_t *__restrict__ id,
@@ -254,6 +287,10 @@ __global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const doub
     }
     const int64_t Kx = a.g.K[0], Ky = a.g.K[1];
     const R qr = (R)q;
+    // FP32 grid: the P x-points of a stencil row are consecutive (k0 - P + 1
+    // .. k0) unless the row wraps at the box edge; add them with vector atomics
+    constexpr bool kVec = sizeof(R) == 4;
+    const bool contiguous = kVec && ix[0][P - 1] + (P - 1) == ix[0][0];
 #pragma unroll
     for (int c = 0; c < P; ++c) {
         const R qz = qr * w[2][c];
@@ -261,6 +298,15 @@ __global__ void __launch_bounds__(kThreads) k_spme_spread(AtomArgs a, const doub
         for (int b = 0; b < P; ++b) {
             const R qzy = qz * w[1][b];
             R *row = grid + ((int64_t)ix[2][c] * Ky + ix[1][b]) * Kx;
+            if constexpr (kVec) {
+                if (contiguous) {
+                    float v[P];
+#pragma unroll
+                    for (int e = 0; e < P; ++e) v[e] = qzy * w[0][P - 1 - e];
+                    red_run<P>(reinterpret_cast<float *>(row + ix[0][P - 1]), v);
+                    continue;
+                }
+            }
 #pragma unroll
             for (int e = 0; e < P; ++e) atomicAdd(row + ix[0][e], qzy * w[0][e]);
         }
