@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-drift", action="store_true")
     ap.add_argument("--no-spme", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--spme-workload", default="coulomb_fcc100_4m")
     return ap.parse_args()
 
@@ -273,6 +274,40 @@ def spme_leg(args, stream, hbm_peak):
         m.close()
     res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     res["hbm_peak_gbs"] = hbm_peak
+    return res
+
+
+def variants_leg(sysd, stream, hbm_peak):
+    """Traversal / list-layout variants of the LJ step on the benchmark
+    workload: the team size of the hierarchical traversal (lanes per atom,
+    which also fixes the list's warp-transposed layout) at 1, 2, 4 and 8.  Per
+    variant: the force kernel's device ms per launch (profiled launches, CUDA
+    events), its HBM fraction over the algorithmic bytes, and the whole step's
+    throughput over two rebuild periods."""
+    import torch
+
+    from paper_2109_09056_b300 import MDSystem
+    res = {"workload": "see config", "axis": "lanes_per_atom", "md_steps": 2 * MD_PER_STEP}
+    for lanes in (1, 2, 4, 8):
+        m = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", rc=sysd.rc,
+                     skin=sysd.skin, dt=sysd.dt, rebuild_every=sysd.rebuild_every,
+                     lanes_per_atom=lanes, stream=stream)
+        m.step(MD_PER_STEP)
+        m.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.step(2 * MD_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        n_force, force_ms, alg = m.profile_read()
+        m.profile(False)
+        m.close()
+        per = force_ms / max(n_force, 1)
+        res[str(lanes)] = {"force_ms_per_launch": per,
+                           "force_hbm_frac": alg / (per * 1e-3) / 1e9 / hbm_peak,
+                           "atom_steps_per_s": sysd.n * 2 * MD_PER_STEP / (e0.elapsed_time(e1) * 1e-3)}
     return res
 
 
@@ -658,6 +693,10 @@ def run_ours(args, dist):
     # ---- long-range Coulomb (SPME) ---------------------------------------------
     if not args.no_spme:
         out["spme"] = spme_leg(args, stream, hbm_peak)
+
+    # ---- traversal / list-layout variants of the LJ step ------------------------
+    if not args.no_variants:
+        out["variants"] = variants_leg(sysd, stream, hbm_peak)
 
     # ---- CPU baseline (oracle) on rank 0 at N = 1 ---------------------------
     cpu = None
