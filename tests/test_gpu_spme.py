@@ -186,3 +186,35 @@ def test_spme_lanes_per_atom(precision, lanes):
     check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, precision)
     sp.close()
     sysm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_grid_as_small_as_the_stencil(precision):
+    """K_d = order..order+2: every stencil row wraps around the grid (several
+    of an atom's points coincide modulo K), the spread's scalar path."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, precision)
+    for order, K in ((8, (8, 9, 10)), (4, (4, 5, 6))):
+        sp = SPME(sysm, cs.q, alpha=0.6, rc=cs.rc, K=K, order=order)
+        check_against_oracle(sysm, sp, cs.q, s.box, 0.6, cs.rc, K, order, precision)
+        sp.close()
+    sysm.close()
+
+
+def test_spme_after_set_state():
+    """Positions replaced through md_set_state: the solver sees the new state
+    (re-sorted, list rebuilt) at its next call."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, "fp64")
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    sp.compute()
+    x2 = s.x + np.random.default_rng(9).uniform(-0.2, 0.2, size=s.x.shape)
+    sysm.set_state(x2, s.v)
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, "fp64")
+    x_now = sysm.state(forces=False)["x"]
+    d = x_now - x2
+    assert np.abs(d - s.box * np.round(d / s.box)).max() <= 1e-12
+    sp.close()
+    sysm.close()
