@@ -372,17 +372,18 @@ __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const doub
     }
 }
 
-// Closing half-kick of velocity Verlet, v += dt/2 F/m (kick = 1), and the
-// kinetic energy of the resulting velocities summed per CTA (fixed order).
+// Closing half-kick of velocity Verlet, v += dt/2 F/m (kick = 1), and, with
+// ke = 1, the kinetic energy of the resulting velocities summed per CTA (fixed
+// order).  kick and ke are uniform over the grid.
 __global__ void __launch_bounds__(kThreads) k_spme_half_kick(const Box *__restrict__ box,
                                                              const Pair *__restrict__ pair,
-                                                             int64_t ns, int kick,
+                                                             int64_t ns, int kick, int ke,
                                                              const int32_t *__restrict__ type,
                                                              const double *__restrict__ f,
                                                              double *__restrict__ v,
                                                              double *__restrict__ part) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double ke = 0.0;
+    double e = 0.0;
     if (i < box[0].n) {
         const int ty = type[i];
         const double hdtm = pair->hdtm[ty], m = pair->mass[ty];
@@ -393,10 +394,10 @@ __global__ void __launch_bounds__(kThreads) k_spme_half_kick(const Box *__restri
                 vv = fma(hdtm, f[d * ns + i], vv);
                 v[d * ns + i] = vv;
             }
-            ke += 0.5 * m * vv * vv;
+            if (ke) e += 0.5 * m * vv * vv;
         }
     }
-    cta_sum_to<kThreads>(ke, part + blockIdx.x);
+    if (ke) cta_sum_to<kThreads>(e, part + blockIdx.x);
 }
 
 template <typename R> struct Cplx;
@@ -1011,7 +1012,8 @@ md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
         }
         st = total_forces(s);
         if (st != MD_OK) return st;
-        k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 1, c->type[c->oc],
+        k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 1,
+                                                       k == nsteps - 1 ? 1 : 0, c->type[c->oc],
                                                        c->f, c->v[c->oc], s->kpart);
         SCK(cudaGetLastError());
         c->ready = true;
@@ -1022,8 +1024,8 @@ md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
     // current velocities when no step ran)
     SCK(launch_finalize(c, MODE_FORCE_ONLY));
     if (nsteps == 0)
-        k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 0, c->type[c->oc],
-                                                       c->f, c->v[c->oc], s->kpart);
+        k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 0, 1,
+                                                       c->type[c->oc], c->f, c->v[c->oc], s->kpart);
     k_spme_sum<<<1, 1024, 0, stream>>>(s->kpart, kb, 0, s->dsum + 2);
     SCK(cudaGetLastError());
     SCK(cudaMemcpyAsync(s->hsum, s->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
