@@ -90,7 +90,7 @@ struct md_spme {
     int64_t ngrid = 0, nhalf = 0;
     double *q = nullptr;        // charges, original atom order (n)
     double *qs = nullptr;       // charge per slot (ns)
-    float *qsf = nullptr;       // FP32 copy per slot (mixed real space)
+    float4 *shq = nullptr;      // mixed: per slot the context's FP32 shadow with w = charge
     bool f32 = false;           // grid precision R: FP32 (mixed context) or FP64
     void *grid = nullptr;       // Q, then dE/dQ: K_z x K_y x K_x of R
     void *ghat = nullptr;       // half spectrum, complex R
@@ -253,17 +253,23 @@ __device__ __forceinline__ void red_run(float *p, const float (&v)[P]) {
     }
 }
 
-// Charge of each slot's atom (gathered by its original id), FP64 and FP32.
+// Charge of each slot's atom (gathered by its original id); for the mixed
+// real-space pass also the slot's FP32 shadow with the charge in w, so that a
+// neighbor costs one 16-byte gather.
 __global__ void __launch_bounds__(kThreads) k_spme_charges(const Box *__restrict__ box, int64_t ns,
                                                            const int32_t *__restrict__ id,
                                                            const double *__restrict__ q_orig,
+                                                           const float4 *__restrict__ sh,
                                                            double *__restrict__ qs,
-                                                           float *__restrict__ qsf) {
+                                                           float4 *__restrict__ shq) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ns || i >= box[0].n) return;
     const double q = q_orig[id[i]];
     qs[i] = q;
-    qsf[i] = (float)q;
+    if (shq) {
+        const float4 p = sh[i];
+        shq[i] = make_float4(p.x, p.y, p.z, (float)q);
+    }
 }
 
 template <int P, typename R>
@@ -452,9 +458,8 @@ __global__ void k_spme_theta(R *__restrict__ theta, const double *__restrict__ b
 struct RealArgs {
     const Box *box;
     const double *r;        // FP64 cell-relative positions (SoA)
-    const float4 *sh;       // FP32 shadow (mixed)
+    const float4 *shq;      // FP32 shadow with w = charge (mixed)
     const double *qs;
-    const float *qsf;
     const int32_t *nn;
     const uint32_t *nbr;
     double *fs;
@@ -498,8 +503,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
         const int nq = (ni - sub + T - 1) / T;
         double F[3];
         if (MIXED) {
-            const float4 si = a.sh[i];
-            const float qi = a.qsf[i];
+            const float4 si = a.shq[i];
+            const float qi = si.w;
             float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
             // kRealBatch entries per lane at a time: their list words, then
             // their shadows and charges, are all in flight before the math
@@ -513,8 +518,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
                     const uint32_t j = e[u] == kSelf ? (uint32_t)i : (e[u] & MD_IDX_MASK);
-                    sj[u] = __ldg(a.sh + j);
-                    qj[u] = e[u] == kSelf ? 0.f : __ldg(a.qsf + j);
+                    sj[u] = __ldg(a.shq + j);
+                    qj[u] = e[u] == kSelf ? 0.f : sj[u].w;
                 }
                 // the batch's terms are summed plainly, then added to the
                 // per-atom sums with one compensated add per component
@@ -645,8 +650,8 @@ cudaError_t launch_real(int T, const RealArgs &ra, int blocks, cudaStream_t st) 
 }
 
 template <int P, typename R>
-cudaError_t launch_atoms(int mode, const AtomArgs &aa, const double *q_orig, double *qs,
-                         float *qsf, void *grid, const double *fs, double *out, cudaStream_t st) {
+cudaError_t launch_atoms(int mode, const AtomArgs &aa, const double *qs, void *grid,
+                         const double *fs, double *out, cudaStream_t st) {
     const int blocks = (int)((aa.ns + kThreads - 1) / kThreads);
     if (mode == kGatherOut)
         k_spme_gather<P, R, false><<<blocks, kThreads, 0, st>>>(aa, qs, (const R *)grid, fs, out);
@@ -658,26 +663,25 @@ cudaError_t launch_atoms(int mode, const AtomArgs &aa, const double *q_orig, dou
 }
 
 template <typename R>
-cudaError_t launch_atoms_p(int p, int mode, const AtomArgs &aa, const double *q_orig, double *qs,
-                           float *qsf, void *grid, const double *fs, double *out, cudaStream_t st) {
+cudaError_t launch_atoms_p(int p, int mode, const AtomArgs &aa, const double *qs, void *grid,
+                           const double *fs, double *out, cudaStream_t st) {
     switch (p) {
-        case 4: return launch_atoms<4, R>(mode, aa, q_orig, qs, qsf, grid, fs, out, st);
-        case 6: return launch_atoms<6, R>(mode, aa, q_orig, qs, qsf, grid, fs, out, st);
-        case 8: return launch_atoms<8, R>(mode, aa, q_orig, qs, qsf, grid, fs, out, st);
+        case 4: return launch_atoms<4, R>(mode, aa, qs, grid, fs, out, st);
+        case 6: return launch_atoms<6, R>(mode, aa, qs, grid, fs, out, st);
+        case 8: return launch_atoms<8, R>(mode, aa, qs, grid, fs, out, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_atoms_any(bool f32, int p, int mode, const AtomArgs &aa, const double *q_orig,
-                             double *qs, float *qsf, void *grid, const double *fs, double *out,
-                             cudaStream_t st) {
-    return f32 ? launch_atoms_p<float>(p, mode, aa, q_orig, qs, qsf, grid, fs, out, st)
-               : launch_atoms_p<double>(p, mode, aa, q_orig, qs, qsf, grid, fs, out, st);
+cudaError_t launch_atoms_any(bool f32, int p, int mode, const AtomArgs &aa, const double *qs,
+                             void *grid, const double *fs, double *out, cudaStream_t st) {
+    return f32 ? launch_atoms_p<float>(p, mode, aa, qs, grid, fs, out, st)
+               : launch_atoms_p<double>(p, mode, aa, qs, grid, fs, out, st);
 }
 
 void destroy(md_spme *s) {
     auto F = [](void *p) { if (p) cudaFree(p); };
-    F(s->q); F(s->qs); F(s->qsf); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part);
+    F(s->q); F(s->qs); F(s->shq); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part);
     F(s->dsum); F(s->fstage); F(s->kpart);
     if (s->hsum) cudaFreeHost(s->hsum);
     if (s->have_fwd) cufftDestroy(s->fwd);
@@ -739,9 +743,9 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     s->nrecip = 4 * (int64_t)c->nsm;
     SCK(salloc(&s->q, n));
     SCK(salloc(&s->qs, ns));
-    SCK(salloc(&s->qsf, ns));
+    if (c->params.precision == MD_MIXED) SCK(salloc(&s->shq, ns));
     SCK(cudaMemset(s->qs, 0, ns * sizeof(double)));   // padding slots stay uncharged
-    SCK(cudaMemset(s->qsf, 0, ns * sizeof(float)));
+    if (s->shq) SCK(cudaMemset(s->shq, 0, ns * sizeof(float4)));
     s->f32 = c->params.precision == MD_MIXED;
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
     SCK(cudaMalloc(&s->grid, s->ngrid * rb));
@@ -855,9 +859,8 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     RealArgs ra;
     ra.box = c->dbox;
     ra.r = c->r[c->pc];
-    ra.sh = c->sh[c->pc];
+    ra.shq = s->shq;
     ra.qs = s->qs;
-    ra.qsf = s->qsf;
     ra.nn = c->nn;
     ra.nbr = c->nbr;
     ra.fs = s->fs;
@@ -885,7 +888,7 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     if (lj) SCK(launch_force(c, MODE_FORCE_ONLY));
     SCK(mark(0));
     k_spme_charges<<<(int)((c->ns + kThreads - 1) / kThreads), kThreads, 0, stream>>>(
-        c->dbox, c->ns, c->id[c->oc], s->q, s->qs, s->qsf);
+        c->dbox, c->ns, c->id[c->oc], s->q, c->sh[c->pc], s->qs, s->shq);
     SCK(cudaGetLastError());
     if (overlap) {
         SCK(cudaEventRecord(s->fork, stream));
@@ -896,8 +899,8 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     }
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
     SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * rb, stream));
-    SCK(launch_atoms_any(s->f32, s->p.order, kSpread, aa, s->q, s->qs, s->qsf, s->grid, nullptr,
-                         nullptr, stream));
+    SCK(launch_atoms_any(s->f32, s->p.order, kSpread, aa, s->qs, s->grid, nullptr, nullptr,
+                         stream));
     SCK(mark(1));
     if (!overlap)
         SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
@@ -924,8 +927,8 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
         FCK(cufftExecZ2D(s->bwd, (cufftDoubleComplex *)s->ghat, (cufftDoubleReal *)s->grid));
     SCK(mark(5));
     if (overlap) SCK(cudaStreamWaitEvent(stream, s->join, 0));
-    SCK(launch_atoms_any(s->f32, s->p.order, acc ? kGatherAcc : kGatherOut, aa, nullptr, s->qs,
-                         nullptr, s->grid, s->fs, out, stream));
+    SCK(launch_atoms_any(s->f32, s->p.order, acc ? kGatherAcc : kGatherOut, aa, s->qs, s->grid,
+                         s->fs, out, stream));
     SCK(mark(6));
     k_spme_sum<<<1, 1024, 0, stream>>>(s->part, real_blocks, s->nrecip, s->dsum);
     SCK(cudaGetLastError());
