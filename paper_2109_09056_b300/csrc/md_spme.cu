@@ -14,10 +14,12 @@
 // memory-bound few tenths of a millisecond of the FP32 pair.
 //
 // One md_spme_compute is these launches on the context's stream:
-//   k_spme_charges  charge of each slot's atom, gathered by its original id;
+//   k_spme_charges  charge of each slot's atom, gathered by its original id
+//                   (mixed: also the slot's shadow with the charge in w);
 //   k_spme_spread   one thread per slot: scaled fractional coordinates from the
 //                   FP64 cell-relative position, order-p spline weights by their
-//                   recursion, p^3 atomic adds into the grid Q;
+//                   recursion, p^3 atomic adds into the grid Q (FP32 grid: each
+//                   stencil row's consecutive points as float4/float2 adds);
 //   k_spme_real     the real-space erfc pairs over the context's Verlet list
 //                   (same warp-transposed rows and lanes per atom as the LJ
 //                   kernels), FP64 or FP32 + Kahan by the context's precision;
@@ -31,8 +33,9 @@
 // then one single-CTA sum of the energy partials (fixed order, deterministic).
 // The real-space pass depends only on the charges: it runs on a side stream,
 // forked after k_spme_charges and joined before the gather, beside the
-// reciprocal chain (it is issue-bound, the chain atomic- and memory-bound).
-// With profiling on, the launches run in order on one stream instead.
+// reciprocal chain (it is issue-bound, the chain atomic- and memory-bound);
+// mixed, as a persistent grid of MD_SPME_REAL_CTAS CTAs per SM.  With
+// profiling on, the launches run in order on one stream instead.
 //
 // md_spme_step integrates Coulomb + LJ with velocity Verlet from the context's
 // non-fused launchers: kick + drift, re-sort and list at the rebuild cadence,
@@ -994,7 +997,12 @@ md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
     if (st != MD_OK) return sfail(s, st, c->err);
     cudaStream_t stream = c->stream;
     const int every = c->params.rebuild_every;
-    const bool prof = s->prof;
+    // per-stage events are for md_spme_compute; steps run the overlapped path
+    struct ProfOff {
+        md_spme *s;
+        bool was;
+        ~ProfOff() { s->prof = was; }
+    } prof_off{s, s->prof};
     s->prof = false;
     // the opening half-kick needs the total force of the current state
     st = total_forces(s);
@@ -1021,7 +1029,6 @@ md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
         SCK(cudaGetLastError());
         c->ready = true;
     }
-    s->prof = prof;
     // energies of the final state: LJ PE from the last force launch's partials,
     // Coulomb from the last SPME sums, KE from the last half-kick (or the
     // current velocities when no step ran)
