@@ -37,13 +37,15 @@
 // mixed, as a persistent grid of MD_SPME_REAL_CTAS CTAs per SM.  With
 // profiling on, the launches run in order on one stream instead.
 //
-// md_spme_step integrates Coulomb + LJ with velocity Verlet from the context's
-// non-fused launchers: kick + drift, re-sort and list at the rebuild cadence,
-// LJ forces (force-only mode), the SPME forces added to them in slot order,
-// then k_spme_half_kick closes the step.
+// md_spme_step integrates Coulomb + LJ with velocity Verlet: the context's
+// kick + drift and its re-sort and list at the rebuild cadence, then one SPME
+// evaluation whose real-space pass is fused with the LJ pair terms (one walk
+// of the list writes F_LJ + F_real; the gather adds F_recip), then
+// k_spme_half_kick closes the step.
 #include <cufft.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <string>
@@ -72,7 +74,9 @@ constexpr int kRealBatch = 4;       // list entries per lane in flight (mixed re
 #ifndef MD_SPME_REAL_CTAS
 #define MD_SPME_REAL_CTAS 4   // the real-space kernel's register-limited residency
 #endif
-constexpr int kRealCtasPerSm = MD_SPME_REAL_CTAS;  // persistent mixed real-space grid
+// persistent mixed real-space grid: this many CTAs per SM, at most the
+// variant's residency (the fused LJ + Coulomb variant holds more registers)
+constexpr int kRealCtasPerSm = MD_SPME_REAL_CTAS;
 constexpr uint32_t kSelf = 0xFFFFFFFFu;  // batch slot past the row's end
 // FP64 real-space pair functions erfc(alpha r) and exp(-alpha^2 r^2) as
 // piecewise polynomials on [0, rc]: kPieces equal intervals, degree kDeg64 in
@@ -110,13 +114,14 @@ struct md_spme {
     double *fs = nullptr;       // real-space forces per slot, SoA 3 x ns
     double *tab64 = nullptr;    // FP64 pair-function polynomials (kTab64)
     double *part = nullptr;     // energy partials: real [nreal], then recip [nrecip]
+    double *lpart = nullptr;    // LJ energy partials of the fused pass [nreal]
     int64_t nreal = 0, nrecip = 0;
-    double *dsum = nullptr;     // 4 doubles: E_real, E_recip, KE (md_spme_step), spare
-    double *hsum = nullptr;     // pinned mirror of dsum, then the LJ PE
-    double *hpe = nullptr;      // = hsum + 4
+    double *dsum = nullptr;     // E_real, E_recip, KE, -, LJ PE, - (md_spme_step fills 2-5)
+    double *hsum = nullptr;     // pinned mirror of dsum
     double *kpart = nullptr;    // kinetic-energy partials of the half-kick
     double *fstage = nullptr;   // n x 3 device output when the caller's f is host memory
     double e_const = 0.0;       // E_self + E_bg
+    int64_t last_real_blocks = 0;  // real-space CTAs (energy partials) of the last pass
     cufftHandle fwd = 0, bwd = 0;
     bool have_fwd = false, have_bwd = false;
     bool prof = false;
@@ -382,8 +387,9 @@ __global__ void __launch_bounds__(kThreads) k_spme_gather(AtomArgs a, const doub
         fr[2] = -q * a.g.kl[2] * (double)gz;
     }
     if (ACC) {
+        // fs null: the real-space forces are in out already (fused LJ pass)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) out[d * a.ns + i] += fs[d * a.ns + i] + fr[d];
+        for (int d = 0; d < 3; ++d) out[d * a.ns + i] += (fs ? fs[d * a.ns + i] : 0.0) + fr[d];
     } else {
         const int64_t g = a.id[i];
 #pragma unroll
@@ -483,6 +489,12 @@ struct RealArgs {
     float alphaf, rc2f, c2af;
     const double *tab64;     // erfc(alpha r), exp(-alpha^2 r^2) pieces (FP64 pass)
     double pinv;             // kPieces / rc
+    // fused LJ + Coulomb pass (md_spme_step): the context's pair tables and
+    // types; fs is then the context's force array and lpart the LJ energy's
+    // per-CTA partials
+    const Pair *pair;
+    const int32_t *type;
+    double *lpart;
 };
 
 // erfc(alpha r) and exp(-alpha^2 r^2) from the piecewise tables (Horner in
@@ -512,15 +524,39 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
 }
 
 // Real-space pairs: U = q_i q_j erfc(alpha r) / r over r^2 < rc^2, full list.
-template <int T, bool MIXED>
+// With LJ, the same walk of the list also takes the LJ 12-6 pair terms of the
+// context (its cutoff, which is at least rc, its eps/sigma tables and shift)
+// and writes F_LJ + F_real: the force pass of a Coulomb + LJ step.
+template <int T, bool MIXED, bool LJ>
 __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
     constexpr int A = 32 / T;
     __shared__ double s_offd[81];
     __shared__ float s_offf[81];
     __shared__ double s_tab64[MIXED ? 1 : kTab64];
+    // LJ tables per type pair: c1 = 24 eps / sigma^2 (FP32) or 24 eps (FP64),
+    // sigma^2, 4 eps, U(rc)
+    __shared__ double s_lj64[LJ && !MIXED ? 4 * 64 : 1];
+    __shared__ float s_lj32[LJ && MIXED ? 4 * 64 : 1];
     const Box &B = a.box[0];
     if (!MIXED)
         for (int k = threadIdx.x; k < kTab64; k += blockDim.x) s_tab64[k] = a.tab64[k];
+    if (LJ && threadIdx.x < 64) {
+        const int k = threadIdx.x;
+        if (MIXED) {
+            s_lj32[k] = a.pair->fc1[k];
+            s_lj32[64 + k] = a.pair->fs2[k];
+            s_lj32[128 + k] = a.pair->fe4[k];
+            s_lj32[192 + k] = a.pair->fush[k];
+        } else {
+            s_lj64[k] = a.pair->e24[k];
+            s_lj64[64 + k] = a.pair->s2[k];
+            s_lj64[128 + k] = a.pair->e4[k];
+            s_lj64[192 + k] = a.pair->ush[k];
+        }
+    }
+    const int nt = LJ ? a.pair->nt : 1;
+    const double rc2lj = LJ ? a.pair->rc2 : 0.0;
+    const float rc2ljf = LJ ? a.pair->rc2f : 0.f;
     if (threadIdx.x < 81) {
         const int code = threadIdx.x / 3, d = threadIdx.x % 3;
         const int o = (d == 0 ? code % 3 : (d == 1 ? (code / 3) % 3 : code / 9)) - 1;
@@ -530,7 +566,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane % T;
-    double pe_lane = 0.0;
+    double pe_lane = 0.0, pl_lane = 0.0;
     for (int64_t wt = (int64_t)blockIdx.x * (kRealBlock / 32) + (threadIdx.x >> 5); wt < a.nwt;
          wt += (int64_t)gridDim.x * (kRealBlock / 32)) {
         const int64_t i = wt * A + lane / T;
@@ -542,7 +578,9 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
         if (MIXED) {
             const float4 si = a.shq[i];
             const float qi = si.w;
+            const int ti = LJ && nt > 1 ? a.type[i] : 0;
             float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+            float pl = 0.f, cl = 0.f;
             // kRealBatch entries per lane at a time: their list words, then
             // their shadows and charges, are all in flight before the math
             for (int k0 = 0; k0 < nq; k0 += kRealBatch) {
@@ -552,15 +590,17 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                     e[u] = k0 + u < nq ? __ldg(row + (size_t)(k0 + u) * 32) : kSelf;
                 float4 sj[kRealBatch];
                 float qj[kRealBatch];
+                int tj[kRealBatch];
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
                     const uint32_t j = e[u] == kSelf ? (uint32_t)i : (e[u] & MD_IDX_MASK);
                     sj[u] = __ldg(a.shq + j);
                     qj[u] = e[u] == kSelf ? 0.f : sj[u].w;
+                    tj[u] = LJ && nt > 1 ? __ldg(a.type + j) : 0;
                 }
                 // the batch's terms are summed plainly, then added to the
                 // per-atom sums with one compensated add per component
-                float bx = 0.f, by = 0.f, bz = 0.f, be = 0.f;
+                float bx = 0.f, by = 0.f, bz = 0.f, be = 0.f, bl = 0.f;
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
                     const int cd = e[u] == kSelf ? 3 * (int)kCodeZero : 3 * (int)(e[u] >> MD_IDX_BITS);
@@ -568,7 +608,28 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                     const float dy = (sj[u].y + s_offf[cd + 1]) - si.y;
                     const float dz = (sj[u].z + s_offf[cd + 2]) - si.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (qj[u] != 0.f && r2 < a.rc2f) {
+                    if (LJ) {
+                        // the LJ cutoff is at least rc: its test covers both
+                        if (e[u] != kSelf && r2 < rc2ljf) {
+                            const float rinv = rsqrtf(r2);
+                            const float r2inv = __frcp_rn(r2);   // s^6, s^12 amplify its error
+                            const int ab = ti * nt + tj[u];
+                            const float q2 = s_lj32[64 + ab] * r2inv;
+                            const float s6 = q2 * q2 * q2;
+                            float g = s_lj32[ab] * q2 * s6 * fmaf(2.f, s6, -1.f);
+                            bl += 0.5f * fmaf(s_lj32[128 + ab] * s6, s6 - 1.f, -s_lj32[192 + ab]);
+                            if (qj[u] != 0.f && r2 < a.rc2f) {
+                                const float qq = qi * qj[u];
+                                const float er = erfcf(a.alphaf * (r2 * rinv));
+                                const float ex = __expf(-(a.alphaf * a.alphaf) * r2);
+                                g = fmaf(qq * fmaf(er, rinv, a.c2af * ex), r2inv, g);
+                                be = fmaf(0.5f * qq, er * rinv, be);
+                            }
+                            bx = fmaf(-g, dx, bx);
+                            by = fmaf(-g, dy, by);
+                            bz = fmaf(-g, dz, bz);
+                        }
+                    } else if (qj[u] != 0.f && r2 < a.rc2f) {
                         const float qq = qi * qj[u];
                         const float rinv = rsqrtf(r2);
                         const float er = erfcf(a.alphaf * (r2 * rinv));
@@ -584,15 +645,18 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 kahan_add(fy, cy, by);
                 kahan_add(fz, cz, bz);
                 kahan_add(pe, cp, be);
+                if (LJ) kahan_add(pl, cl, bl);
             }
             F[0] = (double)(fx - cx);
             F[1] = (double)(fy - cy);
             F[2] = (double)(fz - cz);
             pe_lane += (double)(pe - cp);
+            pl_lane += (double)(pl - cl);
         } else {
             const double rix = a.r[i], riy = a.r[a.ns + i], riz = a.r[2 * a.ns + i];
             const double qi = a.qs[i];
-            double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
+            const int ti = LJ && nt > 1 ? a.type[i] : 0;
+            double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0, pl = 0.0;
             for (int k = 0; k < nq; ++k) {
                 const uint32_t e = __ldg(row + (size_t)k * 32);
                 const uint32_t j = e & MD_IDX_MASK;
@@ -601,22 +665,32 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 const double dy = (__ldg(a.r + a.ns + j) + s_offd[cd + 1]) - riy;
                 const double dz = (__ldg(a.r + 2 * a.ns + j) + s_offd[cd + 2]) - riz;
                 const double r2 = (dx * dx + dy * dy) + dz * dz;
+                double g = 0.0;
+                if (LJ && r2 < rc2lj) {
+                    const double r2inv = 1.0 / r2;
+                    const int ab = ti * nt + (nt > 1 ? __ldg(a.type + j) : 0);
+                    const double q2 = s_lj64[64 + ab] * r2inv;
+                    const double s6 = q2 * q2 * q2;
+                    g = s_lj64[ab] * r2inv * s6 * (2.0 * s6 - 1.0);
+                    pl += 0.5 * (s_lj64[128 + ab] * s6 * (s6 - 1.0) - s_lj64[192 + ab]);
+                }
                 if (r2 < a.rc2) {
                     const double qq = qi * __ldg(a.qs + j);
                     const double rinv = rsqrt(r2);
                     double er, ex;
                     pair_functions<double, kDeg64>(s_tab64, r2 * rinv, a.pinv, er, ex);
-                    const double g = qq * (er * rinv + a.c2a * ex) * (rinv * rinv);
-                    fx -= g * dx;
-                    fy -= g * dy;
-                    fz -= g * dz;
+                    g += qq * (er * rinv + a.c2a * ex) * (rinv * rinv);
                     pe += 0.5 * qq * er * rinv;
                 }
+                fx -= g * dx;
+                fy -= g * dy;
+                fz -= g * dz;
             }
             F[0] = fx;
             F[1] = fy;
             F[2] = fz;
             pe_lane += pe;
+            pl_lane += pl;
         }
 #pragma unroll
         for (int o = T / 2; o; o >>= 1) {
@@ -629,6 +703,10 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
         }
     }
     cta_sum_to<kRealBlock>(pe_lane, a.part + blockIdx.x);
+    if (LJ) {
+        __syncthreads();
+        cta_sum_to<kRealBlock>(pl_lane, a.lpart + blockIdx.x);
+    }
 }
 
 __global__ void k_spme_sum(const double *__restrict__ part, int64_t nreal, int64_t nrecip,
@@ -720,21 +798,60 @@ double fit_pieces(F f, double rc, int deg, double *out) {
     return worst;
 }
 
-template <int T, bool MIXED>
+template <int T, bool MIXED, bool LJ>
 cudaError_t launch_real_t(const RealArgs &ra, int blocks, cudaStream_t st) {
-    k_spme_real<T, MIXED><<<blocks, kRealBlock, 0, st>>>(ra);
+    k_spme_real<T, MIXED, LJ><<<blocks, kRealBlock, 0, st>>>(ra);
     return cudaGetLastError();
 }
 
-template <bool MIXED>
-cudaError_t launch_real(int T, const RealArgs &ra, int blocks, cudaStream_t st) {
+template <bool MIXED, bool LJ>
+cudaError_t launch_real_l(int T, const RealArgs &ra, int blocks, cudaStream_t st) {
     switch (T) {
-        case 1: return launch_real_t<1, MIXED>(ra, blocks, st);
-        case 2: return launch_real_t<2, MIXED>(ra, blocks, st);
-        case 4: return launch_real_t<4, MIXED>(ra, blocks, st);
-        case 8: return launch_real_t<8, MIXED>(ra, blocks, st);
+        case 1: return launch_real_t<1, MIXED, LJ>(ra, blocks, st);
+        case 2: return launch_real_t<2, MIXED, LJ>(ra, blocks, st);
+        case 4: return launch_real_t<4, MIXED, LJ>(ra, blocks, st);
+        case 8: return launch_real_t<8, MIXED, LJ>(ra, blocks, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Resident CTAs per SM of a real-space kernel variant (occupancy API, cached).
+template <int T, bool MIXED, bool LJ>
+int real_residency() {
+    static std::atomic<int> cached{0};
+    int v = cached.load();
+    if (v == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spme_real<T, MIXED, LJ>, kRealBlock,
+                                                          0) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        cached.store(v);
+    }
+    return v;
+}
+
+template <bool MIXED, bool LJ>
+int real_residency_l(int T) {
+    switch (T) {
+        case 1: return real_residency<1, MIXED, LJ>();
+        case 2: return real_residency<2, MIXED, LJ>();
+        case 4: return real_residency<4, MIXED, LJ>();
+        default: return real_residency<8, MIXED, LJ>();
+    }
+}
+
+int real_residency_any(bool mixed, bool lj, int T) {
+    if (mixed) return lj ? real_residency_l<true, true>(T) : real_residency_l<true, false>(T);
+    return lj ? real_residency_l<false, true>(T) : real_residency_l<false, false>(T);
+}
+
+cudaError_t launch_real(bool mixed, bool lj, int T, const RealArgs &ra, int blocks,
+                        cudaStream_t st) {
+    if (mixed) return lj ? launch_real_l<true, true>(T, ra, blocks, st)
+                         : launch_real_l<true, false>(T, ra, blocks, st);
+    return lj ? launch_real_l<false, true>(T, ra, blocks, st)
+              : launch_real_l<false, false>(T, ra, blocks, st);
 }
 
 template <int P, typename R>
@@ -769,7 +886,7 @@ cudaError_t launch_atoms_any(bool f32, int p, int mode, const AtomArgs &aa, cons
 
 void destroy(md_spme *s) {
     auto F = [](void *p) { if (p) cudaFree(p); };
-    F(s->q); F(s->qs); F(s->shq); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part);
+    F(s->q); F(s->qs); F(s->shq); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part); F(s->lpart);
     F(s->dsum); F(s->fstage); F(s->kpart); F(s->tab64);
     if (s->hsum) cudaFreeHost(s->hsum);
     if (s->have_fwd) cufftDestroy(s->fwd);
@@ -841,9 +958,9 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     SCK(cudaMalloc(&s->theta, s->nhalf * rb));
     SCK(salloc(&s->fs, 3 * ns));
     SCK(salloc(&s->part, s->nreal + s->nrecip));
-    SCK(salloc(&s->dsum, 4));
-    SCK(cudaMallocHost(reinterpret_cast<void **>(&s->hsum), 5 * sizeof(double)));
-    s->hpe = s->hsum + 4;
+    SCK(salloc(&s->lpart, s->nreal));
+    SCK(salloc(&s->dsum, 6));
+    SCK(cudaMallocHost(reinterpret_cast<void **>(&s->hsum), 6 * sizeof(double)));
     for (auto &e : s->ev) SCK(cudaEventCreate(&e));
     SCK(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     SCK(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
@@ -936,11 +1053,10 @@ namespace {
 
 // Enqueues one SPME evaluation at the context's current positions on its
 // stream: forces to `out` (original order, n x 3) or, with acc, added to the
-// context's slot-order forces; E_real and E_recip to s->dsum.  With lj, the
-// context's LJ forces are written to its force array first (acc then adds the
-// Coulomb forces to them).  (Measured and dropped: the LJ launch on the side
-// stream beside the reciprocal chain, 1.5% slower per step at 4M atoms: its
-// CTAs fill whole SMs, so nothing runs beside them.)  No host sync.
+// context's slot-order forces; E_real and E_recip to s->dsum.  With lj (a
+// Coulomb + LJ step, acc set), the real-space pass is the fused LJ + Coulomb
+// pass: it writes F_LJ + F_real to the context's force array and the LJ
+// energy's partials to s->lpart, and the gather adds F_recip.  No host sync.
 md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     md_ctx *c = s->ctx;
     const bool mixed = c->params.precision == MD_MIXED;
@@ -978,17 +1094,21 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     ra.c2af = (float)ra.c2a;
     ra.tab64 = s->tab64;
     ra.pinv = kPieces / s->p.rc;
+    ra.pair = c->dpair;
+    ra.type = c->type[c->oc];
+    ra.lpart = s->lpart;
+    if (lj) ra.fs = c->f;
     // beside the reciprocal chain the mixed real-space pass takes a persistent
     // grid of kRealCtasPerSm CTAs per SM (grid-stride over warp tiles), leaving
     // room on every SM for the chain's kernels; the FP64 pass (which dominates
     // its call) and a profiled pass take one warp per tile
     const bool overlap = !s->prof;
     const int64_t tiles_blocks = (ra.nwt + kRealBlock / 32 - 1) / (kRealBlock / 32);
+    const int per_sm = std::min(kRealCtasPerSm, real_residency_any(mixed, lj, c->T));
     const int real_blocks = (int)std::min<int64_t>(
-        tiles_blocks, overlap && mixed ? (int64_t)kRealCtasPerSm * c->nsm : tiles_blocks);
+        tiles_blocks, overlap && mixed ? (int64_t)per_sm * c->nsm : tiles_blocks);
     if (real_blocks > s->nreal) return sfail(s, MD_ERR_ARG, "internal: real-space partials");
 
-    if (lj) SCK(launch_force(c, MODE_FORCE_ONLY));
     SCK(mark(0));
     k_spme_charges<<<(int)((c->ns + kThreads - 1) / kThreads), kThreads, 0, stream>>>(
         c->dbox, c->ns, c->id[c->oc], s->q, c->sh[c->pc], s->qs, s->shq);
@@ -996,18 +1116,16 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     if (overlap) {
         SCK(cudaEventRecord(s->fork, stream));
         SCK(cudaStreamWaitEvent(s->side, s->fork, 0));
-        SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, s->side)
-                  : launch_real<false>(c->T, ra, real_blocks, s->side));
+        SCK(launch_real(mixed, lj, c->T, ra, real_blocks, s->side));
         SCK(cudaEventRecord(s->join, s->side));
     }
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
+    s->last_real_blocks = real_blocks;
     SCK(cudaMemsetAsync(s->grid, 0, s->ngrid * rb, stream));
     SCK(launch_atoms_any(s->f32, s->p.order, kSpread, aa, s->qs, s->grid, nullptr, nullptr,
                          stream));
     SCK(mark(1));
-    if (!overlap)
-        SCK(mixed ? launch_real<true>(c->T, ra, real_blocks, stream)
-                  : launch_real<false>(c->T, ra, real_blocks, stream));
+    if (!overlap) SCK(launch_real(mixed, lj, c->T, ra, real_blocks, stream));
     SCK(mark(2));
     if (s->f32)
         FCK(cufftExecR2C(s->fwd, (cufftReal *)s->grid, (cufftComplex *)s->ghat));
@@ -1031,7 +1149,7 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     SCK(mark(5));
     if (overlap) SCK(cudaStreamWaitEvent(stream, s->join, 0));
     SCK(launch_atoms_any(s->f32, s->p.order, acc ? kGatherAcc : kGatherOut, aa, s->qs, s->grid,
-                         s->fs, out, stream));
+                         lj ? nullptr : s->fs, out, stream));
     SCK(mark(6));
     k_spme_sum<<<1, 1024, 0, stream>>>(s->part, real_blocks, s->nrecip, s->dsum);
     SCK(cudaGetLastError());
@@ -1129,22 +1247,22 @@ md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
         SCK(cudaGetLastError());
         c->ready = true;
     }
-    // energies of the final state: LJ PE from the last force launch's partials,
-    // Coulomb from the last SPME sums, KE from the last half-kick (or the
-    // current velocities when no step ran)
-    SCK(launch_finalize(c, MODE_FORCE_ONLY));
+    // energies of the final state: Coulomb and LJ from the last fused pass and
+    // SPME sums, KE from the last half-kick (or the current velocities when no
+    // step ran)
+    const int64_t real_blocks = s->last_real_blocks;
     if (nsteps == 0)
         k_spme_half_kick<<<kb, kThreads, 0, stream>>>(c->dbox, c->dpair, c->ns, 0, 1,
                                                        c->type[c->oc], c->f, c->v[c->oc], s->kpart);
     k_spme_sum<<<1, 1024, 0, stream>>>(s->kpart, kb, 0, s->dsum + 2);
+    k_spme_sum<<<1, 1024, 0, stream>>>(s->lpart, real_blocks, 0, s->dsum + 4);
     SCK(cudaGetLastError());
-    SCK(cudaMemcpyAsync(s->hsum, s->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    SCK(cudaMemcpyAsync(s->hpe, c->tbox, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaMemcpyAsync(s->hsum, s->dsum, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream));
     st = check_run_flags(c);
     if (st != MD_OK) return sfail(s, st, c->err);
     if (energy) {
         const double ecoul = (s->hsum[0] + s->hsum[1]) + s->e_const;
-        energy[0] = *s->hpe;
+        energy[0] = s->hsum[4];
         energy[1] = ecoul;
         energy[2] = s->hsum[2];
         energy[3] = (energy[0] + energy[1]) + energy[2];

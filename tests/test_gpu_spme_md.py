@@ -41,23 +41,23 @@ def small_charged():
     return s, q
 
 
-def oracle_forces(x, q, s):
+def oracle_forces(x, q, s, shift=False):
     xw = oracle.wrap(x, s.box)[0]
-    f_lj, _, pe = oracle.lj_forces(xw, s.types, s.box)
+    f_lj, _, pe = oracle.lj_forces(xw, s.types, s.box, eps=s.eps, sigma=s.sigma, shift=shift)
     ek, fk = ew.spme_reciprocal(xw, q, s.box, ALPHA, K, ORDER)
     er, fr = ew.ewald_real(xw, q, s.box, ALPHA, RC)
     ec = ek + er + ew.ewald_self(q, ALPHA) + ew.ewald_background(q, s.box, ALPHA)
     return f_lj + fk + fr, pe, ec
 
 
-def oracle_verlet(s, q, nsteps):
+def oracle_verlet(s, q, nsteps, shift=False):
     """Velocity Verlet (m = 1): v += dt/2 F; x += dt v; F = F(x); v += dt/2 F."""
     x, v = s.x.copy(), s.v.copy()
-    f, pe, ec = oracle_forces(x, q, s)
+    f, pe, ec = oracle_forces(x, q, s, shift)
     for _ in range(nsteps):
         v = v + 0.5 * s.dt * f
         x = x + s.dt * v
-        f, pe, ec = oracle_forces(x, q, s)
+        f, pe, ec = oracle_forces(x, q, s, shift)
         v = v + 0.5 * s.dt * f
     return x, v, pe, ec, 0.5 * float((v * v).sum())
 
@@ -125,7 +125,9 @@ def test_spme_step_energy_conservation():
     precisions: no dangerous build (list rebuilt every 0.02 time units), the
     total energy's largest deviation falls with dt^2 (ratio 2.5-6 for dt
     halved) and stays below 1e-4 per atom at dt = 0.002, and the two
-    precisions agree to 1e-6 per atom."""
+    precisions' energy traces agree to a tenth of that deviation (their
+    trajectories drift apart chaotically, so the bar is set by the energy's
+    own integration fluctuation, not by a fixed number)."""
     cs = mi.charged_workload("coulomb_fcc10_4000")
     s = cs.lj
     dev = {}
@@ -145,4 +147,31 @@ def test_spme_step_energy_conservation():
         ratio = dev[prec, 0.004] / dev[prec, 0.002]
         assert 2.5 <= ratio <= 6.0, (prec, ratio)
         assert dev[prec, 0.002] <= 1e-4
-    assert np.abs(dev["fp64", 0.002, "E"] - dev["mixed", 0.002, "E"]).max() <= 1e-6
+    assert (np.abs(dev["fp64", 0.002, "E"] - dev["mixed", 0.002, "E"]).max()
+            <= 0.1 * dev["fp64", 0.002])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_step_two_types_shifted(precision):
+    """The fused LJ + Coulomb pass with two atom types (per-pair eps, sigma in
+    [0.8, 1.2]) and the shifted LJ potential: 12 steps against the oracle loop."""
+    rng = np.random.default_rng(41)
+    s = mi.lj_melt(6, seed=5, jitter=0.1)
+    s.types = np.zeros(s.n, dtype=np.int32)
+    s.types[rng.permutation(s.n)[: s.n // 2]] = 1
+    s.eps, s.sigma = mi.random_pair_params(2, rng)
+    s.mass = np.ones(2)
+    s.rebuild_every = 4
+    q = mi.neutral_charges(s.n, rng)
+    x_o, v_o, pe_o, ec_o, ke_o = oracle_verlet(s, q, 12, shift=True)
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    sysm = make(s, precision, shift_energy=True)
+    sp = SPME(sysm, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    e = sp.step(12)
+    st = sysm.state(forces=False)
+    assert np.linalg.norm(periodic_diff(st["x"], x_o, s.box)) <= tol * np.linalg.norm(x_o)
+    assert rel_l2(st["v"], v_o) <= tol
+    assert abs(e["pe_lj"] - pe_o) <= tol * abs(pe_o)
+    assert abs(e["coulomb"] - ec_o) <= tol * abs(ec_o)
+    sp.close()
+    sysm.close()
