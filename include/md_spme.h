@@ -107,6 +107,8 @@ md_status md_spme_profile_read(md_spme *s, double *ms /* 6 */);
 /* Message of the last failed call on s (NULL: of the last failed create). */
 const char *md_spme_last_error(const md_spme *s);
 
+/* Frees the solver (NULL is a no-op).  It may run after md_destroy of its
+ * context: it uses only its own buffers and the stream handles. */
 void md_spme_destroy(md_spme *s);
 
 #ifdef __cplusplus

@@ -101,6 +101,7 @@ struct Geom {
 
 struct md_spme {
     md_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;  // the context's stream (kept: destroy never reads ctx)
     md_spme_params p{};
     Geom g{};
     int64_t ngrid = 0, nhalf = 0;
@@ -930,6 +931,7 @@ cudaError_t salloc(T **p, size_t count) {
 
 md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) {
     s->ctx = c;
+    s->stream = c->stream;
     s->p = *p;
     const Box &B = c->hbox[0];
     Geom &g = s->g;
@@ -1288,8 +1290,10 @@ const char *md_spme_last_error(const md_spme *s) {
 
 void md_spme_destroy(md_spme *s) {
     if (!s) return;
-    if (s->ctx && s->ctx->stream) cudaStreamSynchronize(s->ctx->stream);
+    // the context may already be gone: only the stream handles are used here
+    if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->side) cudaStreamSynchronize(s->side);
+    cudaGetLastError();
     destroy(s);
     delete s;
 }

@@ -243,3 +243,16 @@ def test_spme_real_space_pair_function_sweep(precision):
         assert np.abs(f - (Fr + Fk)).max() <= tol * (np.abs(Fr).max() + np.abs(Fk).max()), r
         sp.close()
         sysm.close()
+
+
+def test_spme_destroy_after_its_context():
+    """Closing the system before its solver is safe (the solver's destroy
+    touches only its own buffers and stream handles)."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, "mixed")
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    sp.compute()
+    sysm.close()
+    sp.close()
+    torch.cuda.synchronize()
