@@ -77,7 +77,6 @@ constexpr int kRealBatch = 4;       // list entries per lane in flight (mixed re
 // persistent mixed real-space grid: this many CTAs per SM, at most the
 // variant's residency (the fused LJ + Coulomb variant holds more registers)
 constexpr int kRealCtasPerSm = MD_SPME_REAL_CTAS;
-constexpr uint32_t kSelf = 0xFFFFFFFFu;  // batch slot past the row's end
 // FP64 real-space pair functions erfc(alpha r) and exp(-alpha^2 r^2) as
 // piecewise polynomials on [0, rc]: kPieces equal intervals, degree kDeg64 in
 // the interval's local coordinate t in [0, 1).  (B300's FP64 pipe: the
@@ -108,6 +107,7 @@ struct md_spme {
     double *q = nullptr;        // charges, original atom order (n)
     double *qs = nullptr;       // charge per slot (ns)
     float4 *shq = nullptr;      // mixed: per slot the context's FP32 shadow with w = charge
+                                // (ns + 1: the list's sentinel slot ns, far away, w = 0)
     bool f32 = false;           // grid precision R: FP32 (mixed context) or FP64
     void *grid = nullptr;       // Q, then dE/dQ: K_z x K_y x K_x of R
     void *ghat = nullptr;       // half spectrum, complex R
@@ -583,20 +583,23 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
             float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
             float pl = 0.f, cl = 0.f;
             // kRealBatch entries per lane at a time: their list words, then
-            // their shadows and charges, are all in flight before the math
-            for (int k0 = 0; k0 < nq; k0 += kRealBatch) {
+            // their shadows and charges, are all in flight before the math.
+            // Whole batches: the list pad is a multiple of kRealBatch x T and
+            // a row's entries past its count are sentinels, whose slot ns is
+            // far from every atom with no charge.
+            const int nqr = (nq + kRealBatch - 1) & ~(kRealBatch - 1);
+            for (int k0 = 0; k0 < nqr; k0 += kRealBatch) {
                 uint32_t e[kRealBatch];
 #pragma unroll
-                for (int u = 0; u < kRealBatch; ++u)
-                    e[u] = k0 + u < nq ? __ldg(row + (size_t)(k0 + u) * 32) : kSelf;
+                for (int u = 0; u < kRealBatch; ++u) e[u] = __ldg(row + (size_t)(k0 + u) * 32);
                 float4 sj[kRealBatch];
                 float qj[kRealBatch];
                 int tj[kRealBatch];
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
-                    const uint32_t j = e[u] == kSelf ? (uint32_t)i : (e[u] & MD_IDX_MASK);
+                    const uint32_t j = e[u] & MD_IDX_MASK;
                     sj[u] = __ldg(a.shq + j);
-                    qj[u] = e[u] == kSelf ? 0.f : sj[u].w;
+                    qj[u] = sj[u].w;
                     tj[u] = LJ && nt > 1 ? __ldg(a.type + j) : 0;
                 }
                 // the batch's terms are summed plainly, then added to the
@@ -604,14 +607,14 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 float bx = 0.f, by = 0.f, bz = 0.f, be = 0.f, bl = 0.f;
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
-                    const int cd = e[u] == kSelf ? 3 * (int)kCodeZero : 3 * (int)(e[u] >> MD_IDX_BITS);
+                    const int cd = 3 * (int)(e[u] >> MD_IDX_BITS);
                     const float dx = (sj[u].x + s_offf[cd]) - si.x;
                     const float dy = (sj[u].y + s_offf[cd + 1]) - si.y;
                     const float dz = (sj[u].z + s_offf[cd + 2]) - si.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
                     if (LJ) {
                         // the LJ cutoff is at least rc: its test covers both
-                        if (e[u] != kSelf && r2 < rc2ljf) {
+                        if (r2 < rc2ljf) {
                             const float rinv = rsqrtf(r2);
                             const float r2inv = __frcp_rn(r2);   // s^6, s^12 amplify its error
                             const int ab = ti * nt + tj[u];
@@ -950,9 +953,14 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
     s->nrecip = 4 * (int64_t)c->nsm;
     SCK(salloc(&s->q, n));
     SCK(salloc(&s->qs, ns));
-    if (c->params.precision == MD_MIXED) SCK(salloc(&s->shq, ns));
+    if (c->params.precision == MD_MIXED) SCK(salloc(&s->shq, ns + 1));
     SCK(cudaMemset(s->qs, 0, ns * sizeof(double)));   // padding slots stay uncharged
-    if (s->shq) SCK(cudaMemset(s->shq, 0, ns * sizeof(float4)));
+    if (s->shq) {
+        // the sentinel slot ns of the list's padding entries: far away, uncharged
+        SCK(cudaMemset(s->shq, 0, ns * sizeof(float4)));
+        const float4 far = make_float4(1e4f, 1e4f, 1e4f, 0.f);
+        SCK(cudaMemcpy(s->shq + ns, &far, sizeof(float4), cudaMemcpyHostToDevice));
+    }
     s->f32 = c->params.precision == MD_MIXED;
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
     SCK(cudaMalloc(&s->grid, s->ngrid * rb));
