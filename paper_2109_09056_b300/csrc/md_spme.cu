@@ -77,6 +77,12 @@ constexpr int kRealBatch = 4;       // list entries per lane in flight (mixed re
 // persistent mixed real-space grid: this many CTAs per SM, at most the
 // variant's residency (the fused LJ + Coulomb variant holds more registers)
 constexpr int kRealCtasPerSm = MD_SPME_REAL_CTAS;
+#ifndef MD_SPME_FUSED_CTAS
+#define MD_SPME_FUSED_CTAS 3
+#endif
+// the same for the fused LJ + Coulomb pass (its residency at 80 registers;
+// 1/2/3 per SM measured 6.70/4.52/4.42 ms per Coulomb + LJ step at 4M atoms)
+constexpr int kFusedCtasPerSm = MD_SPME_FUSED_CTAS;
 // FP64 real-space pair functions erfc(alpha r) and exp(-alpha^2 r^2) as
 // piecewise polynomials on [0, rc]: kPieces equal intervals, degree kDeg64 in
 // the interval's local coordinate t in [0, 1).  (B300's FP64 pipe: the
@@ -1114,7 +1120,8 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     // its call) and a profiled pass take one warp per tile
     const bool overlap = !s->prof;
     const int64_t tiles_blocks = (ra.nwt + kRealBlock / 32 - 1) / (kRealBlock / 32);
-    const int per_sm = std::min(kRealCtasPerSm, real_residency_any(mixed, lj, c->T));
+    const int per_sm =
+        std::min(lj ? kFusedCtasPerSm : kRealCtasPerSm, real_residency_any(mixed, lj, c->T));
     const int real_blocks = (int)std::min<int64_t>(
         tiles_blocks, overlap && mixed ? (int64_t)per_sm * c->nsm : tiles_blocks);
     if (real_blocks > s->nreal) return sfail(s, MD_ERR_ARG, "internal: real-space partials");
