@@ -11,7 +11,9 @@ dt 0.005, rebuild every 20), mixed precision.  Synthetic, seeded inputs.
 
 Prints one JSON line.  `value` is device-timed (inputs resident in HBM, CUDA
 events on the library's stream); `e2e` goes through the C ABI with pinned HOST
-buffers (state uploaded and read back every step); `roofline` is for the
+buffers (state uploaded and read back every step; the read-back is an
+md_state_stream snapshot copied while the next step runs, and the last one is
+waited for inside the timed region); `roofline` is for the
 dominant kernel (the mixed force kernel) timed live with per-launch CUDA
 events; `cpu_baseline` is the FP64 oracle on the host cores (bounded sample).
 The reference arm (`--impl reference`) times the oracle itself.
@@ -658,17 +660,20 @@ def run_ours(args, dist):
         xo = torch.empty_like(xh).pin_memory()
         vo = torch.empty_like(vh).pin_memory()
         se = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", **common)
+        ss = se.state_stream()
         se.set_state(xh, vh)
         se.step(MD_PER_STEP)
+        ss.push(xo, vo)
+        ss.wait()
         torch.cuda.synchronize()
         dist.barrier()
         t = time.perf_counter()
         for _ in range(args.steps):
             se.set_state(xh, vh)                      # H2D of the step's inputs (x, v)
             se.step(MD_PER_STEP)                      # thermo of the step back to the host
-            A.check(A.lib.md_get_state(se.ctx.handle, A.C.c_void_p(xo.data_ptr()),
-                                       A.C.c_void_p(vo.data_ptr()), None, None, None),
-                    se.ctx.handle)                    # D2H of the step's result (x, v)
+            ss.push(xo, vo)                           # D2H of the step's result (x, v), copied
+                                                      # while the next step runs
+        ss.wait()                                     # the last step's result is on the host
         torch.cuda.synchronize()
         el = dist.max(time.perf_counter() - t)
         dist.barrier()
@@ -676,6 +681,7 @@ def run_ours(args, dist):
                "h2d_bytes_per_step": int(xh.numel() * 8 + vh.numel() * 8),
                "d2h_bytes_per_step": int(xo.numel() * 8 + vo.numel() * 8 + 112),
                "ms_per_step": 1e3 * el / args.steps}
+        ss.close()
         se.close()
 
     # ---- energy drift, mixed vs FP64 ------------------------------------------

@@ -268,6 +268,23 @@ md_status md_info(md_ctx *ctx, int32_t *nbox, int64_t *n_total);
 md_status md_bin_sort_noalloc(const md_box *box, int64_t n, const double *x, double rs,
                               int32_t *perm, void *stream);
 
+/* Asynchronous state download, for trajectory output while the context keeps
+ * stepping.  md_state_stream_push takes a snapshot of x and v (n x 3 FP64,
+ * original atom order) on the context's stream, in stream order, into one of
+ * two library-owned device slots, and queues its copy into x and v (either
+ * may be NULL; host buffers should be pinned for the copy to overlap the
+ * context's work) on the object's own stream; it returns without waiting.
+ * The buffers hold the snapshot once md_state_stream_wait has returned; a slot
+ * is reused only after its previous copy finished.  Errors: MD_ERR_ARG,
+ * MD_ERR_NOMEM, MD_ERR_CUDA; messages via md_state_stream_last_error.  The
+ * object must be destroyed before its context. */
+typedef struct md_state_stream md_state_stream;
+md_status md_state_stream_create(md_ctx *ctx, md_state_stream **out);
+md_status md_state_stream_push(md_state_stream *s, double *x, double *v);
+md_status md_state_stream_wait(md_state_stream *s);
+const char *md_state_stream_last_error(const md_state_stream *s);
+void md_state_stream_destroy(md_state_stream *s);
+
 #ifdef __cplusplus
 }
 #endif

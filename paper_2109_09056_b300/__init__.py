@@ -13,7 +13,9 @@ from .api import (MDSystem, md_batch_create, md_bin_sort_noalloc, md_batch_therm
                   md_get_permutation, md_get_state, md_get_thermo, md_get_thermo_log, md_info,
                   md_debug_expire_waits, md_launch_count, md_params_default, md_profile, md_profile_read, md_profile_rebuild, md_set_params,
                   md_set_positions, md_set_state, md_step, SPME, md_spme_create, md_spme_set_charges,
-                  md_spme_compute, md_spme_step, md_spme_profile, md_spme_profile_read, md_spme_destroy)
+                  md_spme_compute, md_spme_step, md_spme_profile, md_spme_profile_read, md_spme_destroy,
+                  StateStream, md_state_stream_create, md_state_stream_push, md_state_stream_wait,
+                  md_state_stream_destroy)
 from ._native import LIB_PATH, MD_FP64, MD_MIXED, MDError
 
 __all__ = [
@@ -23,7 +25,8 @@ __all__ = [
     "md_get_thermo_log", "md_profile", "md_profile_read", "md_profile_rebuild", "md_destroy", "md_batch_create",
     "md_batch_thermo", "md_info", "md_params_default", "LJForce", "SPME", "md_spme_create",
     "md_spme_set_charges", "md_spme_compute", "md_spme_step", "md_spme_profile", "md_spme_profile_read",
-    "md_spme_destroy",
+    "md_spme_destroy", "StateStream", "md_state_stream_create", "md_state_stream_push",
+    "md_state_stream_wait", "md_state_stream_destroy",
 ]
 
 

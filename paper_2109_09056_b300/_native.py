@@ -96,6 +96,11 @@ SIGNATURES = {
     "md_batch_thermo": ([P, P], C.c_int),
     "md_info": ([P, C.POINTER(C.c_int32), C.POINTER(C.c_int64)], C.c_int),
     "md_bin_sort_noalloc": ([C.POINTER(md_box), C.c_int64, P, C.c_double, P, P], C.c_int),
+    "md_state_stream_create": ([P, C.POINTER(P)], C.c_int),
+    "md_state_stream_push": ([P, P, P], C.c_int),
+    "md_state_stream_wait": ([P], C.c_int),
+    "md_state_stream_last_error": ([P], C.c_char_p),
+    "md_state_stream_destroy": ([P], None),
     # include/md_spme.h
     "md_spme_create": ([P, P, C.POINTER(md_spme_params), C.POINTER(P)], C.c_int),
     "md_spme_set_charges": ([P, P], C.c_int),
@@ -134,6 +139,12 @@ class MDError(RuntimeError):
 def check(status: int, ctx=None) -> None:
     if status != MD_OK:
         msg = lib.md_last_error(ctx)
+        raise MDError(status, msg.decode() if msg else "")
+
+
+def check_io(status: int, obj=None) -> None:
+    if status != MD_OK:
+        msg = lib.md_state_stream_last_error(obj)
         raise MDError(status, msg.decode() if msg else "")
 
 

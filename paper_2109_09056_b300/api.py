@@ -15,7 +15,7 @@ from typing import Optional
 import numpy as np
 
 from . import _native as N
-from ._native import check, check_spme, lib
+from ._native import check, check_io, check_spme, lib
 
 try:
     import torch
@@ -299,6 +299,64 @@ def md_destroy(ctx: Ctx) -> None:
         ctx.handle = C.c_void_p()
 
 
+class StateStream:
+    """Owns an md_state_stream* (asynchronous state download)."""
+
+    def __init__(self, handle: C.c_void_p, ctx: Ctx):
+        self.handle = handle
+        self.ctx = ctx
+
+    def push(self, x=None, v=None) -> None:
+        md_state_stream_push(self, x, v)
+
+    def wait(self) -> None:
+        md_state_stream_wait(self)
+
+    def close(self) -> None:
+        md_state_stream_destroy(self)
+
+    def __del__(self):
+        try:
+            md_state_stream_destroy(self)
+        except Exception:
+            pass
+
+
+def md_state_stream_create(ctx: Ctx) -> StateStream:
+    h = C.c_void_p()
+    check_io(lib.md_state_stream_create(ctx.handle, C.byref(h)))
+    return StateStream(h, ctx)
+
+
+def _out_ptr(a, shape):
+    """Pointer of a caller-owned float64 output (numpy or torch, contiguous)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        assert a.dtype == torch.float64 and a.is_contiguous() and tuple(a.shape) == shape
+        return C.c_void_p(a.data_ptr())
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.shape == shape
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def md_state_stream_push(s: StateStream, x=None, v=None) -> None:
+    """Snapshot x and v now and copy them into the given (n, 3) float64 host
+    (pinned for overlap) or device buffers in the background; they hold the
+    snapshot after md_state_stream_wait."""
+    n = s.ctx.n
+    check_io(lib.md_state_stream_push(s.handle, _out_ptr(x, (n, 3)), _out_ptr(v, (n, 3))), s.handle)
+
+
+def md_state_stream_wait(s: StateStream) -> None:
+    check_io(lib.md_state_stream_wait(s.handle), s.handle)
+
+
+def md_state_stream_destroy(s: StateStream) -> None:
+    if s.handle is not None and s.handle.value:
+        lib.md_state_stream_destroy(s.handle)
+        s.handle = C.c_void_p()
+
+
 class MDSystem:
     """One context (one box, or a batch of boxes) with its parameters."""
 
@@ -374,6 +432,10 @@ class MDSystem:
 
     def profile_read(self):
         return md_profile_read(self.ctx)
+
+    def state_stream(self) -> StateStream:
+        """Asynchronous state download object for this system."""
+        return md_state_stream_create(self.ctx)
 
     def close(self):
         md_destroy(self.ctx)
