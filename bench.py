@@ -11,9 +11,11 @@ dt 0.005, rebuild every 20), mixed precision.  Synthetic, seeded inputs.
 
 Prints one JSON line.  `value` is device-timed (inputs resident in HBM, CUDA
 events on the library's stream); `e2e` goes through the C ABI with pinned HOST
-buffers (state uploaded and read back every step; the read-back is an
-md_state_stream snapshot copied while the next step runs, and the last one is
-waited for inside the timed region); `roofline` is for the
+buffers (state uploaded and read back every step: each step's inputs are
+copied from pinned host memory one step ahead on an upload stream and passed to
+md_set_state as device buffers, each step's result is an md_state_stream
+snapshot copied while the next step runs, and the last one is waited for
+inside the timed region); `roofline` is for the
 dominant kernel (the mixed force kernel) timed live with per-launch CUDA
 events; `cpu_baseline` is the FP64 oracle on the host cores (bounded sample).
 The reference arm (`--impl reference`) times the oracle itself.
@@ -661,19 +663,37 @@ def run_ours(args, dist):
         vo = torch.empty_like(vh).pin_memory()
         se = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", **common)
         ss = se.state_stream()
-        se.set_state(xh, vh)
-        se.step(MD_PER_STEP)
-        ss.push(xo, vo)
-        ss.wait()
+        # each step's inputs are copied from pinned host memory into one of two
+        # device buffers on an upload stream, one step ahead, and handed to
+        # md_set_state as device pointers; the context's stream waits for them
+        up = torch.cuda.Stream(device=dev)
+        xd = [torch.empty_like(xh, device=dev) for _ in range(2)]
+        vd = [torch.empty_like(vh, device=dev) for _ in range(2)]
+        ready = [torch.cuda.Event() for _ in range(2)]
+
+        def upload(k):
+            with torch.cuda.stream(up):
+                xd[k % 2].copy_(xh, non_blocking=True)
+                vd[k % 2].copy_(vh, non_blocking=True)
+                ready[k % 2].record(up)
+
+        def e2e_steps(nsteps):
+            upload(0)
+            for k in range(nsteps):
+                stream.wait_event(ready[k % 2])       # the step's inputs are on the device
+                se.set_state(xd[k % 2], vd[k % 2])    # (md_set_state copies them in and returns)
+                if k + 1 < nsteps:
+                    upload(k + 1)                     # H2D of the next step's inputs, meanwhile
+                se.step(MD_PER_STEP)                  # thermo of the step back to the host
+                ss.push(xo, vo)                       # D2H of the step's result (x, v), copied
+                                                      # while the next step runs
+            ss.wait()                                 # the last step's result is on the host
+
+        e2e_steps(max(args.warmup, 2))                # warm-up: both staging buffers, every copy
         torch.cuda.synchronize()
         dist.barrier()
         t = time.perf_counter()
-        for _ in range(args.steps):
-            se.set_state(xh, vh)                      # H2D of the step's inputs (x, v)
-            se.step(MD_PER_STEP)                      # thermo of the step back to the host
-            ss.push(xo, vo)                           # D2H of the step's result (x, v), copied
-                                                      # while the next step runs
-        ss.wait()                                     # the last step's result is on the host
+        e2e_steps(args.steps)
         torch.cuda.synchronize()
         el = dist.max(time.perf_counter() - t)
         dist.barrier()
