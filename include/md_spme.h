@@ -86,7 +86,11 @@ md_status md_spme_compute(md_spme *s, double *f, double *energy);
  * propagate -> resort) with the total force LJ + Coulomb: per step the
  * context's kick and drift, its re-sort and list rebuild every rebuild_every
  * steps, its LJ forces, the SPME forces added to them, and the closing
- * half-kick.  The forces of the starting state are recomputed first.  energy:
+ * half-kick.  The total forces of the starting state are those this solver's
+ * previous md_spme_step left, if nothing has changed the context since (no
+ * other call launched work on it and its pair parameters are the same), and
+ * are recomputed otherwise.  Library kernels of the solver count in
+ * md_launch_count.  energy:
  * host array of 4 (may be NULL) for the final state: LJ PE, Coulomb energy
  * (real + reciprocal + self + background), kinetic energy, total.  The
  * context's own thermo records keep describing LJ only; after this call

@@ -175,3 +175,40 @@ def test_spme_step_two_types_shifted(precision):
     assert abs(e["coulomb"] - ec_o) <= tol * abs(ec_o)
     sp.close()
     sysm.close()
+
+
+def test_spme_step_reuses_forces_only_while_valid():
+    """Between md_spme_step calls the total forces are reused when nothing
+    touched the context: ten single steps give the trajectory of one call of
+    ten (FP64, 1e-11); md_set_params between two calls is seen (the oracle loop
+    switches eps at the same point), and so is another solver's step."""
+    s, q = small_charged()
+    a = make(s, "fp64")
+    b = make(s, "fp64")
+    sa = SPME(a, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    sb = SPME(b, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    for _ in range(10):
+        sa.step(1)
+    sb.step(10)
+    xa, xb = a.state(forces=False)["x"], b.state(forces=False)["x"]
+    assert np.linalg.norm(periodic_diff(xa, xb, s.box)) <= 1e-11 * np.linalg.norm(xa)
+    # parameters changed between calls: the next call must use the new forces
+    eps2 = np.full((1, 1), 0.8)
+    a.set_params(eps=eps2, sigma=np.ones((1, 1)))
+    sa.step(8)
+    s2 = dataclasses.replace(s, eps=eps2)
+    x1, v1, _, _, _ = oracle_verlet(s, q, 10)
+    x_o, v_o, _, _, _ = oracle_verlet(dataclasses.replace(s2, x=x1, v=v1), q, 8)
+    st = a.state(forces=False)
+    assert np.linalg.norm(periodic_diff(st["x"], x_o, s.box)) <= 1e-9 * np.linalg.norm(x_o)
+    assert rel_l2(st["v"], v_o) <= 1e-9
+    # another solver (other charges) stepping the same context in between
+    sc = SPME(b, -q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    sc.step(0)
+    eb = sb.step(0)
+    e_fresh = SPME(b, q, alpha=ALPHA, rc=RC, K=K, order=ORDER).step(0)
+    assert eb["coulomb"] == pytest.approx(e_fresh["coulomb"], rel=1e-12)
+    for o in (sa, sb, sc):
+        o.close()
+    a.close()
+    b.close()
