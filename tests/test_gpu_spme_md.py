@@ -212,3 +212,28 @@ def test_spme_step_reuses_forces_only_while_valid():
         o.close()
     a.close()
     b.close()
+
+
+@pytest.fixture(scope="module")
+def reference8():
+    s, q = small_charged()
+    return s, q, oracle_verlet(s, q, 8)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_step_lanes_per_atom(reference8, precision, lanes):
+    """The fused LJ + Coulomb pass on every list layout (1, 2, 8 lanes per atom
+    besides the default 4): 8 steps against the oracle loop."""
+    s, q, (x_o, v_o, pe_o, ec_o, ke_o) = reference8
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    sysm = make(s, precision, lanes_per_atom=lanes)
+    sp = SPME(sysm, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    e = sp.step(8)
+    st = sysm.state(forces=False)
+    assert np.linalg.norm(periodic_diff(st["x"], x_o, s.box)) <= tol * np.linalg.norm(x_o)
+    assert rel_l2(st["v"], v_o) <= tol
+    assert abs(e["pe_lj"] - pe_o) <= tol * abs(pe_o)
+    assert abs(e["coulomb"] - ec_o) <= tol * abs(ec_o)
+    sp.close()
+    sysm.close()
