@@ -278,6 +278,19 @@ def spme_leg(args, stream, hbm_peak):
         m.close()
     res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     res["hbm_peak_gbs"] = hbm_peak
+    if not args.no_cpu:
+        # the oracle (numpy FP64: SPME reciprocal part + brute-force real space)
+        # on the small charged box, for scale
+        from oracle import ewald
+        cc = mi.charged_workload("coulomb_fcc10_4000")
+        t = time.perf_counter()
+        ewald.spme_reciprocal(cc.lj.x, cc.q, cc.lj.box, cc.alpha, cc.K, cc.order)
+        ewald.ewald_real(cc.lj.x, cc.q, cc.lj.box, cc.alpha, cc.rc)
+        el = time.perf_counter() - t
+        res["cpu_baseline"] = {"value": cc.lj.n / el, "unit": res["unit"], "kind": "oracle",
+                               "cores": os.cpu_count(),
+                               "sample": "one oracle evaluation of coulomb_fcc10_4000 (4,000 "
+                                         "atoms, 40^3 grid, order 4; numpy)"}
     return res
 
 
