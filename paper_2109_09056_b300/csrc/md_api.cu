@@ -597,6 +597,7 @@ md_status md_batch_create(int32_t nbox, const int64_t *n_per_box, const md_box *
         g_create_error = c->err;
         free_all(c);
         delete c;
+        cudaGetLastError();   // a failed allocation's error is reported, not left pending
         return s;
     }
     *out = c;

@@ -84,7 +84,7 @@ md_status md_state_stream_create(md_ctx *ctx, md_state_stream **out) {
     md_status st = io_init(s, ctx);
     if (st != MD_OK) {
         g_io_error = s->err;
-        io_destroy(s);
+        io_destroy(s);   // also clears a failed allocation's pending error
         delete s;
         return st;
     }

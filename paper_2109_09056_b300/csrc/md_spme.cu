@@ -1058,6 +1058,7 @@ md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md
         g_spme_error = s->err;
         destroy(s);
         delete s;
+        cudaGetLastError();   // a failed allocation's error is reported, not left pending
         return st;
     }
     *out = s;

@@ -136,6 +136,14 @@ def test_spme_argument_checks():
     with pytest.raises(MDError) as ei:
         SPME(sysm, q, alpha=cs.alpha, rc=cs.rc, K=40, order=4)
     assert ei.value.status == 5
+    # a grid too large for the device (4096^3 FP64, 550 GB): the allocation
+    # fails, MD_ERR_NOMEM, and the context stays usable
+    with pytest.raises(MDError) as ei:
+        SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=4096, order=4)
+    assert ei.value.status == 8
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    assert np.isfinite(sp.compute()[0]["total"])
+    sp.close()
     sysm.close()
     # a batched context is refused
     boxes = mi.ensemble(nbox=2, seed=3, n_lo=300, n_hi=400)
