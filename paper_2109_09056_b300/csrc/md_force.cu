@@ -204,7 +204,7 @@ __device__ __forceinline__ void finish_tile(const ForceArgs &a, const SmemTabs &
 // the list words, then the neighbor positions, then the pair terms.
 template <int T, bool ONE, bool THERMO>
 __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs &tb,
-                                             double (*s_offd)[81]) {
+                                             double (*s_offd)[81], float (*s_offf)[81]) {
     constexpr int A = 32 / T;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int sub = lane % T;
@@ -224,6 +224,9 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                 s_offd[wib][3 * lane + 0] = (double)ox * B.h[0];
                 s_offd[wib][3 * lane + 1] = (double)oy * B.h[1];
                 s_offd[wib][3 * lane + 2] = (double)oz * B.h[2];
+                s_offf[wib][3 * lane + 0] = (float)ox * B.hf[0];
+                s_offf[wib][3 * lane + 1] = (float)oy * B.hf[1];
+                s_offf[wib][3 * lane + 2] = (float)oz * B.hf[2];
             }
             __syncwarp();
             curbox = b;
@@ -235,11 +238,49 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
         const int ti = ONE ? 0 : a.type[i];
         double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
         const int nq = (ni - sub + T - 1) / T;
-        for (int q0 = 0; q0 < nq; q0 += kBatch) {
+        // B300's FP64 pipe is charged per warp instruction, however many lanes
+        // are active: the FP64 pass runs only over the entries that can lie
+        // within rc, so that the warp loops over the longest such count rather
+        // than over the longest row.  Pass 1 marks them (FP32 r^2 on the
+        // cell-relative shadows below rc^2 (1 + 1e-4); the shadows' error in r^2
+        // is below 1e-6 rc^2); pass 2 takes them in row order, so the FP64 sums
+        // are those of the full row, term for term.
+        const float4 si = a.sh_in[i];
+        for (int c0 = 0; c0 < nq; c0 += 32) {
+          const int cn = min(32, nq - c0);
+          uint32_t near = 0u;
+          for (int q0 = 0; q0 < cn; q0 += kBatch) {
             uint32_t e[kBatch];
+            float4 sj[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u)
-                e[u] = (q0 + u < nq) ? __ldcs(row + (size_t)(q0 + u) * 32) : kNoEntry;
+                e[u] = (q0 + u < cn) ? __ldg(row + (size_t)(c0 + q0 + u) * 32) : kNoEntry;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                sj[u] = e[u] != kNoEntry ? __ldg(a.sh_in + (e[u] & MD_IDX_MASK))
+                                         : make_float4(1e4f, 1e4f, 1e4f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const float *o = s_offf[wib] + 3 * ((e[u] >> MD_IDX_BITS) % 27);
+                const float dx = (sj[u].x + o[0]) - si.x;
+                const float dy = (sj[u].y + o[1]) - si.y;
+                const float dz = (sj[u].z + o[2]) - si.z;
+                if (e[u] != kNoEntry && dx * dx + dy * dy + dz * dz < a.pair->rc2f * 1.0001f)
+                    near |= 1u << (q0 + u);
+            }
+          }
+          while (near) {
+            uint32_t e[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (near) {
+                    const int k = __ffs(near) - 1;
+                    near &= near - 1u;
+                    e[u] = __ldg(row + (size_t)(c0 + k) * 32);
+                } else {
+                    e[u] = kNoEntry;
+                }
+            }
             double xj[kBatch], yj[kBatch], zj[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
@@ -275,6 +316,7 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                     if (THERMO) pe += 0.5 * (e4 * s6 * (s6 - 1.0) - ush);
                 }
             }
+          }
         }
         const double Fd[3] = {sum_lanes_d<T>(fx), sum_lanes_d<T>(fy), sum_lanes_d<T>(fz)};
         const double ped = THERMO ? sum_lanes_d<T>(pe) : 0.0;
@@ -586,12 +628,13 @@ __global__ void __launch_bounds__(kBlock64, 2) k_force64(ForceArgs a) {
     }
     __shared__ SmemTabs tb;
     __shared__ __align__(16) double s_offd[kMaxWarps][81];
+    __shared__ float s_offf64[kMaxWarps][81];
     load_tabs(*a.pair, tb);
     __syncthreads();
     const int64_t clock = a.fl->clock;
     const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
-    if (thermo) force_body64<T, ONE, true>(a, tb, s_offd);
-    else force_body64<T, ONE, false>(a, tb, s_offd);
+    if (thermo) force_body64<T, ONE, true>(a, tb, s_offd, s_offf64);
+    else force_body64<T, ONE, false>(a, tb, s_offd, s_offf64);
     kernel_done(a, clock, thermo);
 }
 
