@@ -492,6 +492,7 @@ struct RealArgs {
     const Box *box;
     const double *r;        // FP64 cell-relative positions (SoA)
     const float4 *shq;      // FP32 shadow with w = charge (mixed)
+    const float4 *sh;       // the context's FP32 shadow (the FP64 pass's prefilter)
     const double *qs;
     const int32_t *nn;
     const uint32_t *nbr;
@@ -674,7 +675,28 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
             const double qi = a.qs[i];
             const int ti = LJ && nt > 1 ? a.type[i] : 0;
             double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0, pl = 0.0;
-            for (int k = 0; k < nq; ++k) {
+            // The FP64 pipe is charged per warp instruction: an FP32 pass on
+            // the shadows first marks the entries that can lie within the
+            // larger cutoff (r^2 below it by a 1e-4 margin; the shadows' error
+            // in r^2 is below 1e-6 of it), and the FP64 pass takes those only,
+            // in row order (the same sums).
+            const float4 si = a.sh[i];
+            const float cut2 = (float)(LJ ? rc2lj : a.rc2) * 1.0001f;
+            for (int c0 = 0; c0 < nq; c0 += 32) {
+              const int cn = min(32, nq - c0);
+              uint32_t near = 0u;
+              for (int k = 0; k < cn; ++k) {
+                const uint32_t e = __ldg(row + (size_t)(c0 + k) * 32);
+                const float4 sj = __ldg(a.sh + (e & MD_IDX_MASK));
+                const int cd = 3 * (int)(e >> MD_IDX_BITS);
+                const float dx = (sj.x + s_offf[cd]) - si.x;
+                const float dy = (sj.y + s_offf[cd + 1]) - si.y;
+                const float dz = (sj.z + s_offf[cd + 2]) - si.z;
+                if (dx * dx + dy * dy + dz * dz < cut2) near |= 1u << k;
+              }
+              while (near) {
+                const int k = c0 + __ffs(near) - 1;
+                near &= near - 1u;
                 const uint32_t e = __ldg(row + (size_t)k * 32);
                 const uint32_t j = e & MD_IDX_MASK;
                 const int cd = 3 * (int)(e >> MD_IDX_BITS);
@@ -702,6 +724,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 fx -= g * dx;
                 fy -= g * dy;
                 fz -= g * dz;
+              }
             }
             F[0] = fx;
             F[1] = fy;
@@ -1101,6 +1124,7 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     ra.box = c->dbox;
     ra.r = c->r[c->pc];
     ra.shq = s->shq;
+    ra.sh = c->sh[c->pc];
     ra.qs = s->qs;
     ra.nn = c->nn;
     ra.nbr = c->nbr;
