@@ -76,7 +76,8 @@ typedef struct {
     int32_t check_displacement;  /* 1: md_step returns MD_ERR_DANGEROUS_BUILD (see above) */
     int32_t thermo_every;        /* >0: log PE/KE/T/momentum every k steps (md_get_thermo_log) */
     int32_t neigh_pad;           /* list slots per atom; 0 = automatic (grown on overflow) */
-    int32_t lanes_per_atom;      /* 1, 2, 4 or 8 lanes per atom in the force kernel; 0 = auto */
+    int32_t lanes_per_atom;      /* 1, 2, 4 or 8 lanes per atom in the force kernel; 0 = auto
+                                    (4; 1 for MD_FP64 contexts of >= 8192 atoms per SM) */
     int32_t block_threads;       /* mixed force-kernel CTA size (64..768, multiple of 32; an
                                     upper bound when its list buffers would not fit in shared
                                     memory; the FP64 kernel uses at most 256); 0 = automatic

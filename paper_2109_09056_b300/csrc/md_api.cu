@@ -282,7 +282,7 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     c->mass.assign(p.mass, p.mass + p.ntypes);
     for (double m : c->mass)
         if (!(m > 0.0) || !std::isfinite(m)) return fail(c, MD_ERR_ARG, "mass must be > 0");
-    c->T = p.lanes_per_atom ? p.lanes_per_atom : 4;
+    c->T = p.lanes_per_atom ? p.lanes_per_atom : 4;  // automatic: see below for FP64
     if (c->T != 1 && c->T != 2 && c->T != 4 && c->T != 8)
         return fail(c, MD_ERR_ARG, "lanes_per_atom must be 1, 2, 4 or 8");
     c->block = p.block_threads;  // 0: chosen per launch (md_force.cu)
@@ -332,6 +332,12 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+    // Automatic lanes per atom for FP64 contexts: the FP64 pass loops over the
+    // longest per-lane count of entries within rc, which long single-lane rows
+    // balance best, once there are atoms enough for many waves of 32-atom warps
+    // (B300: 4M atoms 2.98e8 atom-steps/s at 1 lane vs 2.86e8 at 4; 131k atoms
+    // 2.44e8 vs 2.71e8, 4,000 atoms 2.6e7 vs 7.8e7).
+    if (!p.lanes_per_atom && p.precision == MD_FP64 && c->n_total >= 8192LL * c->nsm) c->T = 1;
 
     const size_t ns = (size_t)c->ns;
     for (int k = 0; k < 2; ++k) {
