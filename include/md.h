@@ -111,7 +111,8 @@ typedef struct md_ctx md_ctx;
 /* Creates a context for n atoms in one box: copies x, v (n x 3) and types (n,
  * values in [0, ntypes)), then wraps, bins, re-sorts into cell order, builds
  * the neighbor list and computes the forces of step 0.  `stream` is a
- * cudaStream_t (NULL = default stream).  *out receives the context.
+ * cudaStream_t (NULL = default stream).  *out receives the context; on
+ * failure *out is NULL (when out is not NULL).
  * Errors: MD_ERR_ARG, MD_ERR_BOX_TOO_SMALL, MD_ERR_NONFINITE, MD_ERR_NOMEM,
  * MD_ERR_CUDA. */
 md_status md_create(const md_box *box, int64_t n, const double *x, const double *v,

@@ -593,8 +593,8 @@ void md_params_default(md_params *p) {
 md_status md_batch_create(int32_t nbox, const int64_t *n_per_box, const md_box *boxes,
                           const double *x, const double *v, const int32_t *types,
                           const md_params *params, void *stream, md_ctx **out) {
+    if (out) *out = nullptr;
     if (!out || !x) return fail(nullptr, MD_ERR_ARG, "NULL argument");
-    *out = nullptr;
     md_ctx *c = new (std::nothrow) md_ctx();
     if (!c) return fail(nullptr, MD_ERR_NOMEM, "host allocation failed");
     md_status s = init_ctx(c, nbox, n_per_box, boxes, params, stream);
@@ -612,7 +612,10 @@ md_status md_batch_create(int32_t nbox, const int64_t *n_per_box, const md_box *
 
 md_status md_create(const md_box *box, int64_t n, const double *x, const double *v,
                     const int32_t *types, const md_params *params, void *stream, md_ctx **out) {
-    if (n < 1) return fail(nullptr, MD_ERR_ARG, "n must be >= 1");
+    if (n < 1) {
+        if (out) *out = nullptr;
+        return fail(nullptr, MD_ERR_ARG, "n must be >= 1");
+    }
     return md_batch_create(1, &n, box, x, v, types, params, stream, out);
 }
 
