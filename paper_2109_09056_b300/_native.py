@@ -127,7 +127,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     return lib
 
 
-lib = load()
+# MD_B300_LIB may name another build of the same library (the tests' checked
+# build, for instance); the default is the in-tree one
+LIB_PATH_USED = os.environ.get("MD_B300_LIB") or LIB_PATH
+lib = load(LIB_PATH_USED)
 
 
 class MDError(RuntimeError):

@@ -37,7 +37,7 @@ struct AdjArgs {
     double *dx_aos;    // original order
     double *part;      // nwt * NP
     int NP;
-    const Flags *fl;
+    Flags *fl;
 };
 
 __global__ void k_gather_G(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjArgs a) {
         int q = 0;
         for (int k = sub; k < ni; k += T, ++q) {
             const uint32_t e = row[(size_t)q * 32];
-            const int64_t j = e & MD_IDX_MASK;
+            const int64_t j = chk_index(e & MD_IDX_MASK, a.ns, CHK_ADJ_GATHER, a.fl, 0);
             const double *o = s_off[wib] + 3 * (e >> MD_IDX_BITS);
             // d = x_i - x_j
             const double dx = rix - (a.r[j] + o[0]);

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "md_common.cuh"
+#include "md_trace.h"
 
 using namespace mdb;
 
@@ -175,6 +176,16 @@ md_status alloc_list(md_ctx *c, int pad) {
 md_status read_flags(md_ctx *c) {
     CK(cudaMemcpyAsync(c->hflags, c->dflags, sizeof(Flags), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->hflags->check_site != CHK_NONE) {
+        // only a checked build (-DMD_CHECKED) records these
+        static const char *const names[CHK_SITES] = {
+            "none", "sort scatter", "sort permute", "build home atom", "build candidate",
+            "mixed force gather", "FP64 force gather", "adjoint gather", "SPME real-space gather"};
+        const uint32_t k = c->hflags->check_site;
+        return fail(c, MD_ERR_CUDA,
+                    std::string("index check failed: ") + (k < CHK_SITES ? names[k] : "?") +
+                        " (index " + std::to_string(c->hflags->check_index) + ")");
+    }
     return MD_OK;
 }
 
@@ -344,7 +355,9 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
         CK(dalloc(&c->r[k], 3 * ns));
         CK(dalloc(&c->v[k], 3 * ns));
         CK(dalloc(&c->sh[k], ns + 1));   // slot ns: the dummy the sentinel entry points at
-        CK(dalloc(&c->type[k], ns));
+        // slot ns: type 0 for the sentinel entry (read by whole-batch gathers)
+        CK(dalloc(&c->type[k], ns + 1));
+        CK(cudaMemset(c->type[k], 0, (ns + 1) * sizeof(int32_t)));
         CK(dalloc(&c->id[k], ns));
         CK(dalloc(&c->img[k], 3 * ns));
         CK(dalloc(&c->cellc[k], ns));
@@ -593,6 +606,7 @@ void md_params_default(md_params *p) {
 md_status md_batch_create(int32_t nbox, const int64_t *n_per_box, const md_box *boxes,
                           const double *x, const double *v, const int32_t *types,
                           const md_params *params, void *stream, md_ctx **out) {
+    MD_TRACE("md_batch_create");
     if (out) *out = nullptr;
     if (!out || !x) return fail(nullptr, MD_ERR_ARG, "NULL argument");
     md_ctx *c = new (std::nothrow) md_ctx();
@@ -620,6 +634,7 @@ md_status md_create(const md_box *box, int64_t n, const double *x, const double 
 }
 
 md_status md_bin_sort(md_ctx *c) {
+    MD_TRACE("md_bin_sort");
     if (!c) return MD_ERR_ARG;
     if (!c->ready) return fail(c, MD_ERR_ARG, "internal: state between half-steps");
     CK(launch_bin_sort(c, false));
@@ -636,6 +651,7 @@ md_status md_bin_sort(md_ctx *c) {
 }
 
 md_status md_build_neighbors(md_ctx *c) {
+    MD_TRACE("md_build_neighbors");
     if (!c) return MD_ERR_ARG;
     if (c->sorted_at != c->step) {
         // the atoms moved since their cells were assigned: re-sort first, so
@@ -662,6 +678,7 @@ md_status md_build_neighbors(md_ctx *c) {
 }
 
 md_status md_compute_forces(md_ctx *c, double *energy_out) {
+    MD_TRACE("md_compute_forces");
     if (!c) return MD_ERR_ARG;
     if (!c->ready) return fail(c, MD_ERR_ARG, "internal: state between half-steps");
     if (!c->list_valid) {
@@ -740,6 +757,7 @@ static md_status run_period_graph(md_ctx *c) {
 }
 
 md_status md_step(md_ctx *c, int32_t nsteps, md_thermo *last_out) {
+    MD_TRACE("md_step");
     if (!c) return MD_ERR_ARG;
     if (nsteps < 0) return fail(c, MD_ERR_ARG, "nsteps must be >= 0");
     md_status s;
@@ -825,6 +843,7 @@ md_status md_step(md_ctx *c, int32_t nsteps, md_thermo *last_out) {
 }
 
 md_status md_get_state(md_ctx *c, double *x, double *v, double *f, int32_t *img, int32_t *ids) {
+    MD_TRACE("md_get_state");
     if (!c) return MD_ERR_ARG;
     if (f) {
         md_status s = ensure_forces(c);
@@ -858,6 +877,7 @@ md_status md_get_state(md_ctx *c, double *x, double *v, double *f, int32_t *img,
 }
 
 md_status md_get_permutation(md_ctx *c, int32_t *perm) {
+    MD_TRACE("md_get_permutation");
     if (!c || !perm) return MD_ERR_ARG;
     if (c->nbox != 1) return fail(c, MD_ERR_ARG, "md_get_permutation: single-box contexts only");
     const size_t n = (size_t)c->n_total;
@@ -868,6 +888,7 @@ md_status md_get_permutation(md_ctx *c, int32_t *perm) {
 }
 
 md_status md_get_neighbors(md_ctx *c, int32_t *nn, int32_t *nbr, int32_t *pad) {
+    MD_TRACE("md_get_neighbors");
     if (!c) return MD_ERR_ARG;
     if (pad) *pad = c->pad;
     if (!nn && !nbr) return MD_OK;
@@ -923,6 +944,7 @@ md_status md_get_thermo_log(md_ctx *c, double *rows, int32_t *count) {
 
 md_status md_force_backward(md_ctx *c, const double *dL_dF, double dL_dE, double *dL_dx,
                             double *dL_deps, double *dL_dsigma) {
+    MD_TRACE("md_force_backward");
     if (!c || !dL_dF) return MD_ERR_ARG;
     if (c->hpair.nt > 4) return fail(c, MD_ERR_ARG, "md_force_backward supports ntypes <= 4");
     if (!c->ready) return fail(c, MD_ERR_ARG, "internal: state between half-steps");
@@ -975,6 +997,7 @@ md_status md_force_backward(md_ctx *c, const double *dL_dF, double dL_dE, double
 }
 
 md_status md_set_state(md_ctx *c, const double *x, const double *v) {
+    MD_TRACE("md_set_state");
     if (!c) return MD_ERR_ARG;
     if (!x && !v) return MD_OK;
     const size_t n = (size_t)c->n_total;
@@ -1022,6 +1045,7 @@ md_status md_set_positions(md_ctx *c, const double *x) {
 }
 
 md_status md_set_params(md_ctx *c, const double *eps, const double *sigma) {
+    MD_TRACE("md_set_params");
     if (!c) return MD_ERR_ARG;
     const int nt = c->hpair.nt;
     std::vector<double> e(eps ? eps : c->eps.data(), (eps ? eps : c->eps.data()) + nt * nt);

@@ -95,8 +95,57 @@ struct Flags {
     uint32_t maxdisp_bits;  // float bits of max displacement seen by the current re-sort
     uint32_t thermo;        // 1 if the last force launch wrote thermo partials
     uint32_t done;          // CTA completion counter of the force kernel (last-CTA pattern)
-    uint32_t pad_;
+    uint32_t check_site;    // checked build: first failing index check (CheckSite), else 0
+    int64_t check_index;    // checked build: the index that failed it
 };
+
+// Checked build (nvcc -DMD_CHECKED): the hot path's gathers and scatters test
+// each index against the array it addresses.  An index out of range is
+// recorded (the first failing site and its index, in the context's flags);
+// a gather then reads a harmless in-range element instead and a scatter is
+// skipped, and the next host call that reads the flags fails with
+// MD_ERR_CUDA naming the site.  In the default build the checks compile to
+// nothing.
+enum CheckSite : uint32_t {
+    CHK_NONE = 0,
+    CHK_SORT_SCATTER,    // k_scatter: destination slot inside the atom's box
+    CHK_SORT_PERMUTE,    // k_permute: source slot inside the atom's box
+    CHK_BUILD_HOME,      // k_build: home atom slot < ns
+    CHK_BUILD_CAND,      // k_build: candidate slot < ns
+    CHK_FORCE_GATHER,    // mixed force kernels: neighbor shadow slot <= ns
+    CHK_FORCE64_GATHER,  // FP64 force kernel: neighbor slot (< ns for positions)
+    CHK_ADJ_GATHER,      // adjoint kernel: neighbor slot < ns
+    CHK_SPME_GATHER,     // SPME real-space pass: neighbor slot (<= ns shadows, < ns positions)
+    CHK_SITES
+};
+
+// Index i for an access to an array of n elements: i itself when in range,
+// else (checked build) `safe` after recording the failure.
+__device__ __forceinline__ int64_t chk_index(int64_t i, int64_t n, uint32_t site, Flags *fl,
+                                             int64_t safe) {
+#ifdef MD_CHECKED
+    if (i >= 0 && i < n) return i;
+    if (atomicCAS(&fl->check_site, 0u, site) == 0u) fl->check_index = i;
+    return safe;
+#else
+    (void)n; (void)site; (void)fl; (void)safe;
+    return i;
+#endif
+}
+
+// Whether a scatter to index i may go ahead: lo <= i < hi (always true in the
+// default build).
+__device__ __forceinline__ bool chk_ok(int64_t i, int64_t lo, int64_t hi, uint32_t site,
+                                       Flags *fl) {
+#ifdef MD_CHECKED
+    if (i >= lo && i < hi) return true;
+    if (atomicCAS(&fl->check_site, 0u, site) == 0u) fl->check_index = i;
+    return false;
+#else
+    (void)i; (void)lo; (void)hi; (void)site; (void)fl;
+    return true;
+#endif
+}
 
 // Stencil code of a zero offset (ox = oy = oz = 0).
 constexpr uint32_t kCodeZero = 13;

@@ -257,8 +257,10 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                 e[u] = (q0 + u < cn) ? __ldg(row + (size_t)(c0 + q0 + u) * 32) : kNoEntry;
 #pragma unroll
             for (int u = 0; u < kBatch; ++u)
-                sj[u] = e[u] != kNoEntry ? __ldg(a.sh_in + (e[u] & MD_IDX_MASK))
-                                         : make_float4(1e4f, 1e4f, 1e4f, 0.f);
+                sj[u] = e[u] != kNoEntry
+                            ? __ldg(a.sh_in + chk_index(e[u] & MD_IDX_MASK, a.ns + 1,
+                                                        CHK_FORCE64_GATHER, a.fl, a.ns))
+                            : make_float4(1e4f, 1e4f, 1e4f, 0.f);
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const float *o = s_offf[wib] + 3 * ((e[u] >> MD_IDX_BITS) % 27);
@@ -284,15 +286,15 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
             double xj[kBatch], yj[kBatch], zj[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                const uint32_t j = e[u] & MD_IDX_MASK;
                 const bool ok = e[u] != kNoEntry;
+                const int64_t j =
+                    ok ? chk_index(e[u] & MD_IDX_MASK, a.ns, CHK_FORCE64_GATHER, a.fl, 0) : 0;
                 xj[u] = ok ? __ldg(a.r_in + j) : 1e4;
                 yj[u] = ok ? __ldg(a.r_in + a.ns + j) : 1e4;
                 zj[u] = ok ? __ldg(a.r_in + 2 * a.ns + j) : 1e4;
             }
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                const uint32_t j = e[u] & MD_IDX_MASK;
                 const double *o = s_offd[wib] + 3 * ((e[u] >> MD_IDX_BITS) % 27);
                 const double dx = (xj[u] + o[0]) - rix;
                 const double dy = (yj[u] + o[1]) - riy;
@@ -303,6 +305,8 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                     if (ONE) {
                         e24 = de24_0; s2 = ds2_0; e4 = de4_0; ush = dush_0;
                     } else {
+                        const int64_t j =
+                            chk_index(e[u] & MD_IDX_MASK, a.ns, CHK_FORCE64_GATHER, a.fl, 0);
                         const int ab = ti * nt + __ldg(a.type + j);
                         e24 = tb.de24[ab]; s2 = tb.ds2[ab]; e4 = tb.de4[ab]; ush = tb.dush[ab];
                     }
@@ -535,12 +539,15 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             for (int u = 0; u < kBatch; ++u) eb[u] = Lr[(q + u) * 32];
             float4 sj[kBatch];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) sj[u] = __ldg(a.sh_in + (eb[u] & MD_IDX_MASK));
+            for (int u = 0; u < kBatch; ++u)
+                sj[u] = __ldg(a.sh_in + chk_index(eb[u] & MD_IDX_MASK, a.ns + 1, CHK_FORCE_GATHER,
+                                                  a.fl, a.ns));
             batch(eb, sj);
         }
         for (int q = rows_full; q < rows_cur; ++q) {
             const uint32_t en = Lr[q * 32];
-            const float4 sj = __ldg(a.sh_in + (en & MD_IDX_MASK));
+            const float4 sj = __ldg(a.sh_in + chk_index(en & MD_IDX_MASK, a.ns + 1,
+                                                        CHK_FORCE_GATHER, a.fl, a.ns));
             float tx, ty, tz, tp;
             terms(en, sj, tx, ty, tz, tp);
             kahan_add(fx, cx, tx);

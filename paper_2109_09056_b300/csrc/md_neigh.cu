@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
     for (int hb = 0; hb < hm; hb += 32) {
         const int nh = min(32, hm - hb);
         const bool active = lane < nh;
-        const int64_t i = h0 + hb + (active ? lane : 0);  // this lane's home atom
+        const int64_t i = chk_index(h0 + hb + (active ? lane : 0), a.ns, CHK_BUILD_HOME, a.fl,
+                                    0);  // this lane's home atom
         const uint32_t self_meta = (uint32_t)i | (kCodeZero << MD_IDX_BITS);
         const float4 si = a.sh[i];
         __syncwarp();
@@ -181,7 +182,8 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
                     bool keep = false;
                     float4 q = far;
                     if (g < hi_s) {
-                        const int64_t j = s_start[w][s] + (g - s_pref[w][s]);
+                        const int64_t j = chk_index(s_start[w][s] + (g - s_pref[w][s]), a.ns,
+                                                    CHK_BUILD_CAND, a.fl, 0);
                         const float4 p = a.sh[j];
                         q = make_float4(p.x + ox, p.y + oy, p.z + oz,
                                         __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));

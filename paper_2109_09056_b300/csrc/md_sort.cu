@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_out(const int32_t *__rest
 __global__ void k_scatter(const Box *__restrict__ boxes, const int32_t *__restrict__ tile_box,
                           int64_t ns, const int32_t *__restrict__ cell,
                           const int32_t *__restrict__ rank, const int32_t *__restrict__ cstart,
-                          int32_t *__restrict__ ptmp, const Flags *fl) {
+                          int32_t *__restrict__ ptmp, Flags *fl) {
     if (fl->status & ST_FREEZE) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ns) return;
@@ -219,7 +219,8 @@ __global__ void k_scatter(const Box *__restrict__ boxes, const int32_t *__restri
     if (i - B.slot_off >= B.n) return;
     int32_t c = cell[i];
     int64_t slot = B.slot_off + ((int64_t)cstart[c] - B.atom_base) + rank[i];
-    ptmp[slot] = (int32_t)i;
+    if (chk_ok(slot, B.slot_off, (int64_t)B.slot_off + B.n, CHK_SORT_SCATTER, fl))
+        ptmp[slot] = (int32_t)i;
 }
 
 // One warp per cell: rank each slot's prior index among the cell's slots.
@@ -254,7 +255,7 @@ __global__ void k_permute(const Box *__restrict__ boxes, const int32_t *__restri
                           int32_t *__restrict__ img_out, int32_t *__restrict__ cellc_out,
                           const int32_t *__restrict__ cellc_in,
                           float4 *__restrict__ sh_out, double *__restrict__ rbuild,
-                          double *__restrict__ xws, int32_t *__restrict__ nn, const Flags *fl) {
+                          double *__restrict__ xws, int32_t *__restrict__ nn, Flags *fl) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= ns) return;
     if (fl->status & ST_FREEZE) {
@@ -285,7 +286,8 @@ __global__ void k_permute(const Box *__restrict__ boxes, const int32_t *__restri
         nn[k] = 0;
         return;
     }
-    const int32_t old = perm[k];
+    const int32_t old = (int32_t)(B.slot_off + chk_index((int64_t)perm[k] - B.slot_off, B.n,
+                                                         CHK_SORT_PERMUTE, fl, k - B.slot_off));
     const int32_t loc = cell[old] - B.cell_off;
     const int cx = loc % B.nc[0], cy = (loc / B.nc[0]) % B.nc[1], cz = loc / (B.nc[0] * B.nc[1]);
     const int cc[3] = {cx, cy, cz};

@@ -53,6 +53,7 @@
 #include <vector>
 
 #include "md_common.cuh"
+#include "md_trace.h"
 #include "md_spme.h"
 
 namespace mdb {  // md_api.cu
@@ -510,6 +511,7 @@ struct RealArgs {
     const Pair *pair;
     const int32_t *type;
     double *lpart;
+    Flags *fl;               // the context's flags (index checks of a checked build)
 };
 
 // erfc(alpha r) and exp(-alpha^2 r^2) from the piecewise tables (Horner in
@@ -611,7 +613,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 int tj[kRealBatch];
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
-                    const uint32_t j = e[u] & MD_IDX_MASK;
+                    const int64_t j =
+                        chk_index(e[u] & MD_IDX_MASK, a.ns + 1, CHK_SPME_GATHER, a.fl, a.ns);
                     sj[u] = __ldg(a.shq + j);
                     qj[u] = sj[u].w;
                     tj[u] = LJ && nt > 1 ? __ldg(a.type + j) : 0;
@@ -687,7 +690,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
               uint32_t near = 0u;
               for (int k = 0; k < cn; ++k) {
                 const uint32_t e = __ldg(row + (size_t)(c0 + k) * 32);
-                const float4 sj = __ldg(a.sh + (e & MD_IDX_MASK));
+                const float4 sj = __ldg(
+                    a.sh + chk_index(e & MD_IDX_MASK, a.ns + 1, CHK_SPME_GATHER, a.fl, a.ns));
                 const int cd = 3 * (int)(e >> MD_IDX_BITS);
                 const float dx = (sj.x + s_offf[cd]) - si.x;
                 const float dy = (sj.y + s_offf[cd + 1]) - si.y;
@@ -698,7 +702,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 const int k = c0 + __ffs(near) - 1;
                 near &= near - 1u;
                 const uint32_t e = __ldg(row + (size_t)k * 32);
-                const uint32_t j = e & MD_IDX_MASK;
+                const int64_t j = chk_index(e & MD_IDX_MASK, a.ns, CHK_SPME_GATHER, a.fl, 0);
                 const int cd = 3 * (int)(e >> MD_IDX_BITS);
                 const double dx = (__ldg(a.r + j) + s_offd[cd]) - rix;
                 const double dy = (__ldg(a.r + a.ns + j) + s_offd[cd + 1]) - riy;
@@ -1061,6 +1065,7 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
 extern "C" {
 
 md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md_spme **out) {
+    MD_TRACE("md_spme_create");
     if (!out) return sfail(nullptr, MD_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!c || !q || !p) return sfail(nullptr, MD_ERR_ARG, "NULL argument");
@@ -1145,6 +1150,7 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     ra.pair = c->dpair;
     ra.type = c->type[c->oc];
     ra.lpart = s->lpart;
+    ra.fl = c->dflags;
     if (lj) ra.fs = c->f;
     // beside the reciprocal chain the mixed real-space pass takes a persistent
     // grid of kRealCtasPerSm CTAs per SM (grid-stride over warp tiles), leaving
@@ -1227,6 +1233,7 @@ md_status total_forces(md_spme *s) { return enqueue(s, s->ctx->f, true, true); }
 extern "C" {
 
 md_status md_spme_compute(md_spme *s, double *f, double *energy) {
+    MD_TRACE("md_spme_compute");
     if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
     md_ctx *c = s->ctx;
     md_status st = ensure_list(c);
@@ -1258,6 +1265,7 @@ md_status md_spme_compute(md_spme *s, double *f, double *energy) {
 }
 
 md_status md_spme_step(md_spme *s, int32_t nsteps, double *energy) {
+    MD_TRACE("md_spme_step");
     if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
     if (nsteps < 0) return sfail(s, MD_ERR_ARG, "nsteps must be >= 0");
     md_ctx *c = s->ctx;
