@@ -92,9 +92,10 @@ struct SmemTabs {
 
 // The velocity-Verlet epilogue for component d of atom i; returns the new
 // shadow coordinate (FUSED) and accumulates thermo terms.
-template <bool THERMO>
+template <bool THERMO, bool PRE>
 __device__ __forceinline__ float epilogue(const ForceArgs &a, const SmemTabs &tb, int64_t i, int d,
-                                          int ti, double F, double &ke, double &p, double &disp2) {
+                                          int ti, double F, double pv, double pr, double &ke,
+                                          double &p, double &disp2) {
     const int64_t o = d * a.ns + i;
     float snew = 0.f;
     if (a.mode == MODE_FORCE_ONLY) {
@@ -120,8 +121,8 @@ __device__ __forceinline__ float epilogue(const ForceArgs &a, const SmemTabs &tb
         // streaming accesses (read or written once per step): keep them out of
         // L1, which holds the neighbor shadows the gathers reuse
         double vv;
-        const double v0 = __ldcs(a.v + o);
-        const double r0 = __ldcs(a.r_in + o);
+        const double v0 = PRE ? pv : __ldcs(a.v + o);
+        const double r0 = PRE ? pr : __ldcs(a.r_in + o);
         if (THERMO) {
             const double vh = fma(tb.hdtm[ti], F, v0);
             ke += 0.5 * tb.mass[ti] * vh * vh;
@@ -141,13 +142,39 @@ __device__ __forceinline__ float epilogue(const ForceArgs &a, const SmemTabs &tb
 }
 
 
+// A lane's FP64 state for the FUSED velocity-Verlet epilogue: components
+// d = sub + k T (k < NC) of velocity and position, loaded when a tile starts
+// so that their DRAM latency overlaps the tile's list rows instead of
+// stalling the epilogue.
+template <int T>
+struct TileState {
+    static constexpr int NC = (3 + T - 1) / T;
+    double v[NC], r[NC];
+};
+
+template <int T>
+__device__ __forceinline__ void load_tile_state(const ForceArgs &a, int64_t i, bool valid,
+                                                TileState<T> &st) {
+    const int sub = (threadIdx.x & 31) % T;
+#pragma unroll
+    for (int k = 0; k < TileState<T>::NC; ++k) {
+        const int d = sub + k * T;
+        const bool on = valid && d < 3 && a.mode == MODE_FUSED;
+        const int64_t o = (int64_t)(on ? d : 0) * a.ns + i;
+        st.v[k] = on ? __ldcs(a.v + o) : 0.0;
+        st.r[k] = on ? __ldcs(a.r_in + o) : 0.0;
+    }
+}
+
 // The rest of a warp-tile once each atom's force is known in all its lanes:
-// the velocity-Verlet epilogue (lane `sub` takes components sub, sub + T, ...),
-// the atom's next shadow, and the tile's thermo partials.
-template <int T, bool THERMO, typename FT>
+// the velocity-Verlet epilogue (lane `sub` takes components sub, sub + T, ...;
+// PRE: with the state `st` loaded at the tile's start), the atom's next
+// shadow, and the tile's thermo partials.  Only the components a lane handles
+// are widened to FP64.
+template <int T, bool THERMO, bool PRE, typename FT>
 __device__ __forceinline__ void finish_tile(const ForceArgs &a, const SmemTabs &tb, int64_t wt,
                                             int64_t i, bool valid, int ti, const FT (&F)[3],
-                                            double ped) {
+                                            double ped, const TileState<T> &st) {
     const int lane = threadIdx.x & 31, sub = lane % T;
     double ke = 0.0, pd[3] = {0.0, 0.0, 0.0}, disp2 = 0.0;
     float snew[3] = {0.f, 0.f, 0.f};
@@ -157,7 +184,8 @@ __device__ __forceinline__ void finish_tile(const ForceArgs &a, const SmemTabs &
         if (valid && d < 3) {
             const double Fc = (double)(d == 0 ? F[0] : (d == 1 ? F[1] : F[2]));
             double pp = 0.0;
-            const float sn = epilogue<THERMO>(a, tb, i, d, ti, Fc, ke, pp, disp2);
+            const float sn =
+                epilogue<THERMO, PRE>(a, tb, i, d, ti, Fc, st.v[k], st.r[k], ke, pp, disp2);
 #pragma unroll
             for (int dd = 0; dd < 3; ++dd)
                 if (dd == d) { snew[dd] = sn; pd[dd] = pp; }
@@ -324,7 +352,8 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
         }
         const double Fd[3] = {sum_lanes_d<T>(fx), sum_lanes_d<T>(fy), sum_lanes_d<T>(fz)};
         const double ped = THERMO ? sum_lanes_d<T>(pe) : 0.0;
-        finish_tile<T, THERMO>(a, tb, wt, i, valid, ti, Fd, ped);
+        const TileState<T> none{};
+        finish_tile<T, THERMO, false>(a, tb, wt, i, valid, ti, Fd, ped, none);
     }
 }
 
@@ -389,15 +418,19 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 // Wait for the mbarrier phase of the given parity; false after ~1 s (or 2^28
-// polls), so a copy that never completes cannot hang the kernel.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
+// polls), so a copy that never completes cannot hang the kernel.  The first
+// poll is inlined (a tile's rows were requested a whole tile earlier and have
+// nearly always landed); the bounded loop is a call.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity) {
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t k = 1; k < (1u << 28); ++k) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((k & 255u) == 0u && globaltimer_ns() - t0 > 1000000000ull) return false;
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
 // List rows a warp-tile needs: its longest row (rows past an atom's count hold
@@ -437,9 +470,13 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     __syncwarp();
     int64_t wt = t0 + wib;
     int rows_cur = 0;
+    int nn_next = 0;  // the next tile's count for this lane's atom, loaded a tile ahead
+    float4 si_next = make_float4(0.f, 0.f, 0.f, 0.f);  // the next tile's home shadow, likewise
     if (wt < t1) {
         rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
         if (lane == 0) bulk_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, bar0, pol, a.tx_extra);
+        if (wt + nwc < t1) nn_next = __ldg(a.nn + (wt + nwc) * A + lane / T);
+        si_next = a.sh_in[wt * A + lane / T];
     }
     int cb = 0;
     int curbox = -1;
@@ -448,11 +485,13 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         const bool has_next = wn < t1;
         int rows_next = 0;
         if (has_next) {
-            rows_next = tile_rows<T>(min(__ldg(a.nn + wn * A + lane / T), a.pad));
+            rows_next = tile_rows<T>(min(nn_next, a.pad));
             if (lane == 0)
                 bulk_rows(sbuf0 + (cb ^ 1) * bstride, a.nbr + wn * rowblk, rows_next,
                           bar0 + 8 * (cb ^ 1), pol, a.tx_extra);
         }
+        // the count of the tile after next, in flight while this tile runs
+        nn_next = wn + nwc < t1 ? __ldg(a.nn + (wn + nwc) * A + lane / T) : 0;
         const int64_t i = wt * A + lane / T;
         const int b = a.tile_box[(wt * A) >> 5];
         const Box &B = a.boxes[b];
@@ -465,8 +504,11 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             curbox = b;
         }
         const bool valid = (i - B.slot_off) < B.n;
-        const float4 si = a.sh_in[i];
+        const float4 si = si_next;
+        if (has_next) si_next = a.sh_in[wn * A + lane / T];
         const int ti = ONE ? 0 : __float_as_int(si.w);
+        TileState<T> st;
+        load_tile_state<T>(a, i, valid, st);
         // the current tile's rows have landed; a wait that runs out abandons
         // the step with a timeout status (after waiting, again bounded, for
         // the copy in flight into the other half)
@@ -558,10 +600,10 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         __syncwarp();  // done reading this half; the next copy may refill it
         // each lane folds its compensation (value = s - c); the T lane
         // partials of an atom are then added in a fixed xor-shuffle order
-        const double Fd[3] = {(double)sum_lanes_f<T>(fx - cx), (double)sum_lanes_f<T>(fy - cy),
-                              (double)sum_lanes_f<T>(fz - cz)};
+        const float Ff[3] = {sum_lanes_f<T>(fx - cx), sum_lanes_f<T>(fy - cy),
+                             sum_lanes_f<T>(fz - cz)};
         const double ped = THERMO ? (double)sum_lanes_f<T>(pe - cp) : 0.0;
-        finish_tile<T, THERMO>(a, tb, wt, i, valid, ti, Fd, ped);
+        finish_tile<T, THERMO, true>(a, tb, wt, i, valid, ti, Ff, ped, st);
         cb ^= 1;
         rows_cur = rows_next;
     }
