@@ -264,6 +264,15 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
         const uint32_t *row = a.nbr + (size_t)wt * a.R * 32 + lane;
         const double rix = a.r_in[i], riy = a.r_in[a.ns + i], riz = a.r_in[2 * a.ns + i];
         const int ti = ONE ? 0 : a.type[i];
+        // the epilogue's velocities, in flight during the rows (positions: rix..)
+        TileState<T> st;
+#pragma unroll
+        for (int k = 0; k < TileState<T>::NC; ++k) {
+            const int d = sub + k * T;
+            const bool on = valid && d < 3 && a.mode == MODE_FUSED;
+            st.v[k] = on ? __ldcs(a.v + (int64_t)(on ? d : 0) * a.ns + i) : 0.0;
+            st.r[k] = d == 0 ? rix : (d == 1 ? riy : riz);
+        }
         double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
         const int nq = (ni - sub + T - 1) / T;
         // B300's FP64 pipe is charged per warp instruction, however many lanes
@@ -352,8 +361,7 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
         }
         const double Fd[3] = {sum_lanes_d<T>(fx), sum_lanes_d<T>(fy), sum_lanes_d<T>(fz)};
         const double ped = THERMO ? sum_lanes_d<T>(pe) : 0.0;
-        const TileState<T> none{};
-        finish_tile<T, THERMO, false>(a, tb, wt, i, valid, ti, Fd, ped, none);
+        finish_tile<T, THERMO, true>(a, tb, wt, i, valid, ti, Fd, ped, st);
     }
 }
 
