@@ -515,8 +515,11 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         const float4 si = si_next;
         if (has_next) si_next = a.sh_in[wn * A + lane / T];
         const int ti = ONE ? 0 : __float_as_int(si.w);
+        // one lane per atom holds three components: there the registers are
+        // worth more to the rows (long ones) than the early loads
+        constexpr bool kPre = T >= 2;
         TileState<T> st;
-        load_tile_state<T>(a, i, valid, st);
+        if (kPre) load_tile_state<T>(a, i, valid, st);
         // the current tile's rows have landed; a wait that runs out abandons
         // the step with a timeout status (after waiting, again bounded, for
         // the copy in flight into the other half)
@@ -611,7 +614,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         const float Ff[3] = {sum_lanes_f<T>(fx - cx), sum_lanes_f<T>(fy - cy),
                              sum_lanes_f<T>(fz - cz)};
         const double ped = THERMO ? (double)sum_lanes_f<T>(pe - cp) : 0.0;
-        finish_tile<T, THERMO, true>(a, tb, wt, i, valid, ti, Ff, ped, st);
+        finish_tile<T, THERMO, kPre>(a, tb, wt, i, valid, ti, Ff, ped, st);
         cb ^= 1;
         rows_cur = rows_next;
     }
