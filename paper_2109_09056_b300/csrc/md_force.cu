@@ -480,7 +480,11 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
     int rows_cur = 0;
     int nn_next = 0;  // the next tile's count for this lane's atom, loaded a tile ahead
     float4 si_next = make_float4(0.f, 0.f, 0.f, 0.f);  // the next tile's home shadow, likewise
+    int b_next = 0;  // and its box
+    int64_t box_slot = 0;
+    int32_t box_n = 0;
     if (wt < t1) {
+        b_next = a.tile_box[(wt * A) >> 5];
         rows_cur = tile_rows<T>(min(__ldg(a.nn + wt * A + lane / T), a.pad));
         if (lane == 0) bulk_rows(sbuf0, a.nbr + wt * rowblk, rows_cur, bar0, pol, a.tx_extra);
         if (wt + nwc < t1) nn_next = __ldg(a.nn + (wt + nwc) * A + lane / T);
@@ -501,17 +505,21 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         // the count of the tile after next, in flight while this tile runs
         nn_next = wn + nwc < t1 ? __ldg(a.nn + (wn + nwc) * A + lane / T) : 0;
         const int64_t i = wt * A + lane / T;
-        const int b = a.tile_box[(wt * A) >> 5];
-        const Box &B = a.boxes[b];
+        const int b = b_next;
+        if (has_next) b_next = a.tile_box[(wn * A) >> 5];
         if (b != curbox) {
-            // offset of stencil code `lane` (codes 27..31 unused: zero)
+            // offset of stencil code `lane` (codes 27..31 unused: zero), and
+            // the box's slot range
+            const Box &B = a.boxes[b];
             const bool code = lane < 27;
             s_off[wib][0][lane] = code ? (float)(lane % 3 - 1) * B.hf[0] : 0.f;
             s_off[wib][1][lane] = code ? (float)((lane / 3) % 3 - 1) * B.hf[1] : 0.f;
             s_off[wib][2][lane] = code ? (float)(lane / 9 - 1) * B.hf[2] : 0.f;
+            box_slot = B.slot_off;
+            box_n = B.n;
             curbox = b;
         }
-        const bool valid = (i - B.slot_off) < B.n;
+        const bool valid = (i - box_slot) < box_n;
         const float4 si = si_next;
         if (has_next) si_next = a.sh_in[wn * A + lane / T];
         const int ti = ONE ? 0 : __float_as_int(si.w);
