@@ -606,7 +606,8 @@ def run_ours(args, dist):
             from paper_2109_09056_b300.tune import autotune
             t_tune = time.perf_counter()
             res = autotune(factory, nb, key="lj_ensemble_512", periods=1, lanes=(2, 4, 8),
-                           blocks=(128, 256, 768), pad_slack=(8, 16), cadences=(10, 15, 20))
+                           blocks=(128, 256, 768), pad_slack=(8, 16), cadences=(10, 15, 20),
+                           skins=(None, 0.4))
             tuned = res["params"]
             tune_s = time.perf_counter() - t_tune
         sb = factory(**tuned)

@@ -1,6 +1,7 @@
 """Autotuner for the MD step: picks lanes per atom (which fixes the list
 layout), the force kernel's CTA size, the list padding, and the rebuild
-cadence, by timing short runs of the real workload on the current GPU.
+cadence with the list skin, by timing short runs of the real workload on the
+current GPU.
 
     from paper_2109_09056_b300.tune import autotune
     best = autotune(factory, n_atoms, cache="~/.cache/md_b300_tune.json")
@@ -12,10 +13,14 @@ given keyword overrides; the tuner never looks inside it.
 Search: (1) every (lanes_per_atom, block_threads) pair with the automatic
 pad, timed over `periods` rebuild periods after a warm-up period; (2) for the
 winner, list pads of max-row + {8, 16, 32} slots against the automatic pad;
-(3) rebuild cadences: a cadence is safe when no atom moved more than skin/2
-between two builds during the trial (the list then provably holds every pair
-closer than rc); the fastest safe cadence wins, and if none is safe the
-smallest candidate is kept.  Results are cached per (workload key, GPU name).
+(3) rebuild cadences, for each candidate skin (default: the factory's own):
+a cadence is safe when no atom moved more than skin/2 between two builds
+during the trial (the list then provably holds every pair closer than rc); the
+fastest safe (skin, cadence) wins, and if none is safe the smallest cadence is
+kept.  A larger skin lengthens every row (by ((rc + skin') / (rc + skin))^3)
+but makes longer cadences safe; the forces are the same for any skin, so it is
+a pure speed trade.  A trial with another skin goes back to the automatic pad.
+Results are cached per (workload key, GPU name).
 """
 from __future__ import annotations
 
@@ -76,7 +81,8 @@ def cadence_safe(res: dict) -> bool:
 def autotune(factory: Callable, n_atoms: int, key: str = "", cache: str | None = None,
              periods: int = 2, lanes: Iterable[int] = LANES, blocks: Iterable[int] = BLOCKS,
              pad_slack: Iterable[int] = PAD_SLACK, cadences: Iterable[int] = CADENCES,
-             timer: Callable = time_config, log: Callable = lambda *a: None) -> dict:
+             skins: Iterable = (None,), timer: Callable = time_config,
+             log: Callable = lambda *a: None) -> dict:
     """Tune and return {"params": {...}, "rate": atom-steps/s, "trials": [...]}."""
     cache_key = f"{key}|n={n_atoms}|gpu={_gpu_name()}"
     if cache:
@@ -109,8 +115,14 @@ def autotune(factory: Callable, n_atoms: int, key: str = "", cache: str | None =
         for s in pad_slack:
             stage2.append(run(dict(best_p, neigh_pad=nn_max + s), base_every))
     best_p, best_r = choose(stage2)
-    # (3) cadence: fastest among the safe ones, else the smallest
-    stage3 = [run(best_p, e) for e in cadences]
+    # (3) cadence x skin: fastest among the safe ones, else the smallest cadence
+    stage3 = []
+    for sk in skins:
+        p3 = dict(best_p)
+        if sk is not None:
+            p3["skin"] = sk
+            p3.pop("neigh_pad", None)
+        stage3 += [run(p3, e) for e in cadences]
     pick = choose(stage3, cadence_safe)
     if pick is None:
         pick = min(stage3, key=lambda pr: pr[0]["rebuild_every"])

@@ -43,6 +43,25 @@ def test_cache_hit_skips_trials(tmp_path):
     assert again["params"] == first["params"]
 
 
+def test_skin_axis_trades_row_length_for_cadence():
+    # a larger skin: every row longer (slower per step) but cadence 20 safe
+    def timer(factory, params, periods, steps, n):
+        skin = params.get("skin", 0.3)
+        rate = 1e9 * (1.0 + 0.02 * params["rebuild_every"]) * (0.95 if skin > 0.3 else 1.0)
+        danger = int(params["rebuild_every"] > (20 if skin > 0.3 else 15))
+        return {"rate": rate, "ms": 1.0, "thermo": {"dangerous_builds": danger, "nn_max": 90}}
+    out = tune.autotune(None, 1000, key="s", timer=timer, skins=(None, 0.4), cadences=(10, 15, 20))
+    p = out["params"]
+    assert p["skin"] == 0.4 and p["rebuild_every"] == 20 and "neigh_pad" not in p
+    # when the longer rows cost more than the cadence saves, the default skin stays
+    def slow(factory, params, periods, steps, n):
+        r = timer(factory, params, periods, steps, n)
+        r["rate"] *= 0.5 if params.get("skin", 0.3) > 0.3 else 1.0
+        return r
+    out = tune.autotune(None, 1000, key="s2", timer=slow, skins=(None, 0.4), cadences=(10, 15, 20))
+    assert "skin" not in out["params"] and out["params"]["rebuild_every"] == 15
+
+
 def test_no_safe_cadence_keeps_smallest():
     def always_danger(factory, params, periods, steps, n):
         r = fake_timer(factory, params, periods, steps, n)
