@@ -91,8 +91,10 @@ constexpr int kFusedCtasPerSm = MD_SPME_FUSED_CTAS;
 // library erfc and exp were 78% of the FP64 pass; the tables cut it 70.7 ->
 // 31.1 ms at 4M atoms.  In FP32 the same tables, read with divergent interval
 // indices, were 2% slower than erfcf and the exp intrinsic, which stay.)
-constexpr int kPieces = 32;
-constexpr int kDeg64 = 10;
+// 64 pieces of degree 8 meet the fit's 1e-14 bar wherever 32 of degree 10 did
+// (alpha rc up to ~10; host check at create) with 4 fewer DFMAs per pair.
+constexpr int kPieces = 64;
+constexpr int kDeg64 = 8;
 constexpr int kTab64 = 2 * kPieces * (kDeg64 + 1);
 constexpr int kEvents = 7;
 enum { kSpread = 0, kGatherOut = 1, kGatherAcc = 2 };
