@@ -96,6 +96,16 @@ constexpr int kFusedCtasPerSm = MD_SPME_FUSED_CTAS;
 constexpr int kPieces = 64;
 constexpr int kDeg64 = 8;
 constexpr int kTab64 = 2 * kPieces * (kDeg64 + 1);
+// Mixed pass: erfc(x) = exp(-x^2) t H(s) on [0, alpha rc], with t = 1 / (1 + p x)
+// (the form of Hastings' erfc approximations, Abramowitz & Stegun 7.1.26),
+// s = (t - t_min) / (1 - t_min) in [0, 1] and H of degree kErfcDeg interpolated
+// at Chebyshev nodes on the host for the solver's own range; the kernel reuses
+// the exp(-x^2) that the force needs.  (B300, 4M atoms: erfcf was ~0.3 ms of a
+// 4.3 ms Coulomb + LJ step.)  Used when its FP32 evaluation is within
+// kErfcTol of erfc over the range, else erfcf.
+constexpr int kErfcDeg = 7;
+constexpr double kErfcP = 0.47;
+constexpr double kErfcTol = 1e-6;
 constexpr int kEvents = 7;
 enum { kSpread = 0, kGatherOut = 1, kGatherAcc = 2 };
 
@@ -124,6 +134,9 @@ struct md_spme {
     void *theta = nullptr;      // influence function on the half spectrum, R
     double *fs = nullptr;       // real-space forces per slot, SoA 3 x ns
     double *tab64 = nullptr;    // FP64 pair-function polynomials (kTab64)
+    float erfc_c[kErfcDeg + 1] = {};  // mixed: H's coefficients in s (see kErfcDeg)
+    float erfc_sa = 0.f, erfc_sb = 0.f;  // s = sa t + sb
+    bool erfc_fit = false;      // H met kErfcTol (else erfcf)
     double *part = nullptr;     // energy partials: real [nreal], then recip [nrecip]
     double *lpart = nullptr;    // LJ energy partials of the fused pass [nreal]
     int64_t nreal = 0, nrecip = 0;
@@ -505,6 +518,8 @@ struct RealArgs {
     int R, pad;
     double alpha, rc2, c2a;  // c2a = 2 alpha / sqrt(pi)
     float alphaf, rc2f, c2af;
+    float ec[kErfcDeg + 1], esa, esb;  // erfc(x) = exp(-x^2) t H(sa t + sb) when efit
+    int efit;
     const double *tab64;     // erfc(alpha r), exp(-alpha^2 r^2) pieces (FP64 pass)
     double pinv;             // kPieces / rc
     // fused LJ + Coulomb pass (md_spme_step): the context's pair tables and
@@ -515,6 +530,18 @@ struct RealArgs {
     double *lpart;
     Flags *fl;               // the context's flags (index checks of a checked build)
 };
+
+// erfc(x) for the mixed real-space pass, ex = exp(-x^2) from the caller: the
+// host-fitted form when it met its accuracy check, else the library erfcf.
+__device__ __forceinline__ float erfc_mixed(const RealArgs &a, float x, float ex) {
+    if (!a.efit) return erfcf(x);
+    const float t = __fdividef(1.0f, fmaf((float)kErfcP, x, 1.0f));
+    const float sv = fmaf(a.esa, t, a.esb);
+    float h = a.ec[kErfcDeg];
+#pragma unroll
+    for (int k = kErfcDeg - 1; k >= 0; --k) h = fmaf(h, sv, a.ec[k]);
+    return ex * (t * h);
+}
 
 // erfc(alpha r) and exp(-alpha^2 r^2) from the piecewise tables (Horner in
 // the interval's local coordinate t = r kPieces / rc - k), D the degree.
@@ -643,8 +670,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                             bl += 0.5f * fmaf(s_lj32[128 + ab] * s6, s6 - 1.f, -s_lj32[192 + ab]);
                             if (qj[u] != 0.f && r2 < a.rc2f) {
                                 const float qq = qi * qj[u];
-                                const float er = erfcf(a.alphaf * (r2 * rinv));
                                 const float ex = __expf(-(a.alphaf * a.alphaf) * r2);
+                                const float er = erfc_mixed(a, a.alphaf * (r2 * rinv), ex);
                                 g = fmaf(qq * fmaf(er, rinv, a.c2af * ex), r2inv, g);
                                 be = fmaf(0.5f * qq, er * rinv, be);
                             }
@@ -655,8 +682,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                     } else if (qj[u] != 0.f && r2 < a.rc2f) {
                         const float qq = qi * qj[u];
                         const float rinv = rsqrtf(r2);
-                        const float er = erfcf(a.alphaf * (r2 * rinv));
                         const float ex = __expf(-(a.alphaf * a.alphaf) * r2);
+                        const float er = erfc_mixed(a, a.alphaf * (r2 * rinv), ex);
                         const float g = qq * fmaf(er, rinv, a.c2af * ex) * (rinv * rinv);
                         bx = fmaf(-g, dx, bx);
                         by = fmaf(-g, dy, by);
@@ -793,6 +820,43 @@ bool spline_moduli(int p, int K, double *out) {
     return true;
 }
 
+// Degree n - 1 interpolant of g on [0, 1] at the Chebyshev nodes, as
+// monomial coefficients in t (out[0..n-1], Horner order out[n-1] ... out[0]).
+template <typename G>
+void cheb_fit01(G g, int n, double *out) {
+    const double pi = 3.141592653589793;
+    std::vector<double> y(n), c(n, 0.0), mono(n, 0.0);
+    for (int m = 0; m < n; ++m) {
+        const double x = std::cos(pi * (m + 0.5) / n);        // node in [-1, 1]
+        y[m] = g(0.5 * (x + 1.0));
+    }
+    for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int m = 0; m < n; ++m) acc += y[m] * std::cos(pi * j * (m + 0.5) / n);
+        c[j] = (j == 0 ? 1.0 : 2.0) * acc / n;
+    }
+    // T_j(2t - 1) as polynomials in t: T_0 = 1, T_1 = 2t - 1,
+    // T_{j+1} = (4t - 2) T_j - T_{j-1}
+    std::vector<double> tm(n, 0.0), t0(n, 0.0), t1(n, 0.0);
+    t0[0] = 1.0;
+    if (n > 1) {
+        t1[0] = -1.0;
+        t1[1] = 2.0;
+    }
+    for (int i = 0; i < n; ++i) mono[i] += c[0] * t0[i];
+    for (int j = 1; j < n; ++j) {
+        for (int i = 0; i < n; ++i) mono[i] += c[j] * t1[i];
+        std::fill(tm.begin(), tm.end(), 0.0);
+        for (int i = 0; i < n; ++i) {
+            tm[i] += -2.0 * t1[i] - t0[i];
+            if (i + 1 < n) tm[i + 1] += 4.0 * t1[i];
+        }
+        t0.swap(t1);
+        t1.swap(tm);
+    }
+    for (int i = 0; i < n; ++i) out[i] = mono[i];
+}
+
 // Piecewise polynomial of f on [0, rc]: on each of kPieces equal intervals,
 // Chebyshev interpolation at the deg + 1 first-kind nodes, re-expressed in the
 // monomial basis of the local coordinate t in [0, 1) (out[piece * (deg + 1) +
@@ -800,40 +864,12 @@ bool spline_moduli(int p, int K, double *out) {
 // points per interval.
 template <typename F>
 double fit_pieces(F f, double rc, int deg, double *out) {
-    const double pi = 3.141592653589793, w = rc / kPieces;
+    const double w = rc / kPieces;
     const int n = deg + 1;
     double worst = 0.0;
     for (int k = 0; k < kPieces; ++k) {
-        std::vector<double> y(n), c(n, 0.0), mono(n, 0.0);
-        for (int m = 0; m < n; ++m) {
-            const double x = std::cos(pi * (m + 0.5) / n);        // node in [-1, 1]
-            y[m] = f((k + 0.5 * (x + 1.0)) * w);
-        }
-        for (int j = 0; j < n; ++j) {
-            double acc = 0.0;
-            for (int m = 0; m < n; ++m) acc += y[m] * std::cos(pi * j * (m + 0.5) / n);
-            c[j] = (j == 0 ? 1.0 : 2.0) * acc / n;
-        }
-        // T_j(2t - 1) as polynomials in t: T_0 = 1, T_1 = 2t - 1,
-        // T_{j+1} = (4t - 2) T_j - T_{j-1}
-        std::vector<double> tm(n, 0.0), t0(n, 0.0), t1(n, 0.0);
-        t0[0] = 1.0;
-        if (n > 1) {
-            t1[0] = -1.0;
-            t1[1] = 2.0;
-        }
-        for (int i = 0; i < n; ++i) mono[i] += c[0] * t0[i];
-        for (int j = 1; j < n; ++j) {
-            for (int i = 0; i < n; ++i) mono[i] += c[j] * t1[i];
-            std::fill(tm.begin(), tm.end(), 0.0);
-            for (int i = 0; i < n; ++i) {
-                tm[i] += -2.0 * t1[i] - t0[i];
-                if (i + 1 < n) tm[i + 1] += 4.0 * t1[i];
-            }
-            t0.swap(t1);
-            t1.swap(tm);
-        }
-        for (int i = 0; i < n; ++i) out[k * n + i] = mono[i];
+        double *mono = out + k * n;
+        cheb_fit01([&](double t) { return f((k + t) * w); }, n, mono);
         for (int q = 0; q <= 64; ++q) {
             const double t = q / 64.0;
             double v = mono[n - 1];
@@ -842,6 +878,37 @@ double fit_pieces(F f, double rc, int deg, double *out) {
         }
     }
     return worst;
+}
+
+// Mixed real-space pass: H(s) of erfc(x) = exp(-x^2) t H(s) on [0, alpha rc]
+// (kErfcDeg), then the check of its FP32 evaluation against erfc.
+void fit_erfc_mixed(md_spme *s, double alpha, double rc) {
+    const double X = alpha * rc * (1.0 + 1e-6);
+    const double tmin = 1.0 / (1.0 + kErfcP * X);
+    const int n = kErfcDeg + 1;
+    std::vector<double> mono(n);
+    cheb_fit01(
+        [&](double sv) {
+            const double t = tmin + (1.0 - tmin) * sv;
+            const double x = (1.0 / t - 1.0) / kErfcP;
+            return std::erfc(x) * std::exp(x * x) / t;
+        },
+        n, mono.data());
+    for (int k = 0; k < n; ++k) s->erfc_c[k] = (float)mono[k];
+    s->erfc_sa = (float)(1.0 / (1.0 - tmin));
+    s->erfc_sb = (float)(-tmin / (1.0 - tmin));
+    double worst = 0.0;
+    for (int q = 0; q <= 4000; ++q) {
+        const float xf = (float)(X * q / 4000.0);
+        const float t = 1.0f / std::fmaf((float)kErfcP, xf, 1.0f);
+        const float sv = std::fmaf(s->erfc_sa, t, s->erfc_sb);
+        float h = s->erfc_c[kErfcDeg];
+        for (int k = kErfcDeg - 1; k >= 0; --k) h = std::fmaf(h, sv, s->erfc_c[k]);
+        const float ex = (float)std::exp(-(double)xf * (double)xf);
+        const double ref = std::erfc((double)xf);
+        worst = std::max(worst, std::fabs((double)(ex * (t * h)) - ref) / ref);
+    }
+    s->erfc_fit = worst <= kErfcTol;
 }
 
 template <int T, bool MIXED, bool LJ>
@@ -1053,6 +1120,7 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
         SCK(salloc(&s->tab64, kTab64));
         SCK(cudaMemcpy(s->tab64, h64.data(), kTab64 * sizeof(double), cudaMemcpyHostToDevice));
     }
+    if (s->f32) fit_erfc_mixed(s, p->alpha, p->rc);
     FCK(cufftPlan3d(&s->fwd, g.K[2], g.K[1], g.K[0], s->f32 ? CUFFT_R2C : CUFFT_D2Z));
     s->have_fwd = true;
     FCK(cufftPlan3d(&s->bwd, g.K[2], g.K[1], g.K[0], s->f32 ? CUFFT_C2R : CUFFT_Z2D));
@@ -1148,6 +1216,10 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     ra.rc2f = (float)ra.rc2;
     ra.c2af = (float)ra.c2a;
     ra.tab64 = s->tab64;
+    for (int k = 0; k <= kErfcDeg; ++k) ra.ec[k] = s->erfc_c[k];
+    ra.esa = s->erfc_sa;
+    ra.esb = s->erfc_sb;
+    ra.efit = s->erfc_fit ? 1 : 0;
     ra.pinv = kPieces / s->p.rc;
     ra.pair = c->dpair;
     ra.type = c->type[c->oc];
