@@ -230,7 +230,7 @@ def test_spme_after_set_state():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_spme_real_space_pair_function_sweep(precision):
-    """The real-space pair terms across [0, rc): a +-1 dimer at separations
+    """The real-space pair terms across [0, rc): a +-1 dimer at 24 separations
     from 0.05 to just below the cutoff (LJ off, eps = 0), energy and force of
     the real-space part against erfc evaluated by the oracle (scipy): relative
     1e-12 (FP64) / 2e-6 (mixed)."""
@@ -238,7 +238,9 @@ def test_spme_real_space_pair_function_sweep(precision):
     L, alpha, rc = 10.0, 1.25, 2.5
     tol = 1e-12 if precision == "fp64" else 2e-6
     q = np.array([1.0, -1.0])
-    for r in (0.05, 0.3, 0.7, 1.0, 1.37, 1.9, 2.3, 2.45, 2.499):
+    # 24 separations: the mixed pass's erfc is a fitted polynomial form on
+    # [0, alpha rc], so its interior is sampled too, not only the ends
+    for r in sorted(set(np.round(np.linspace(0.05, 2.45, 22), 6)) | {2.499, 1.37}):
         x = np.array([[3.0, 4.0, 5.0], [3.0 + r * 0.6, 4.0 + r * 0.8, 5.0]])
         sysm = MDSystem(x, np.zeros((2, 3)), np.zeros(2, np.int32), np.full(3, L),
                         eps=np.zeros((1, 1)), precision=precision, stream=torch.cuda.Stream())
