@@ -531,6 +531,14 @@ struct RealArgs {
     Flags *fl;               // the context's flags (index checks of a checked build)
 };
 
+// 1/x from the approximate reciprocal and one Newton-Raphson step
+// (r' = r + r (1 - x r)): within about an ulp, where the LJ powers of the fused
+// pass need more than the approximation alone gives.
+__device__ __forceinline__ float rcp_newton(float x) {
+    const float r = __fdividef(1.0f, x);
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
 // erfc(x) for the mixed real-space pass, ex = exp(-x^2) from the caller: the
 // host-fitted form when it met its accuracy check, else the library erfcf.
 __device__ __forceinline__ float erfc_mixed(const RealArgs &a, float x, float ex) {
@@ -662,7 +670,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                         // the LJ cutoff is at least rc: its test covers both
                         if (r2 < rc2ljf) {
                             const float rinv = rsqrtf(r2);
-                            const float r2inv = __frcp_rn(r2);   // s^6, s^12 amplify its error
+                            const float r2inv = rcp_newton(r2);  // s^6, s^12 amplify its error
                             const int ab = ti * nt + tj[u];
                             const float q2 = s_lj32[64 + ab] * r2inv;
                             const float s6 = q2 * q2 * q2;
