@@ -1174,6 +1174,8 @@ md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md
 md_status md_spme_set_charges(md_spme *s, const double *q) {
     if (!s) return sfail(nullptr, MD_ERR_ARG, "NULL solver");
     if (!q) return sfail(s, MD_ERR_ARG, "q is NULL");
+    // the total forces a previous md_spme_step left belong to the old charges
+    s->f_step = -1;
     return load_charges(s, q);
 }
 

@@ -181,7 +181,8 @@ def test_spme_step_reuses_forces_only_while_valid():
     """Between md_spme_step calls the total forces are reused when nothing
     touched the context: ten single steps give the trajectory of one call of
     ten (FP64, 1e-11); md_set_params between two calls is seen (the oracle loop
-    switches eps at the same point), and so is another solver's step."""
+    switches eps at the same point), and so are another solver's step and
+    md_spme_set_charges."""
     s, q = small_charged()
     a = make(s, "fp64")
     b = make(s, "fp64")
@@ -212,6 +213,25 @@ def test_spme_step_reuses_forces_only_while_valid():
         o.close()
     a.close()
     b.close()
+    # new charges between two calls: the opening half-kick must use the forces
+    # of the new charges (the oracle loop switches q at the same point), and the
+    # energy of a zero-step call must be that of a fresh solver with them
+    c = make(s, "fp64")
+    sd = SPME(c, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    sd.step(3)
+    q2 = np.roll(q, 1) * 0.5
+    sd.set_charges(q2)
+    e0 = sd.step(0)
+    e_new = SPME(c, q2, alpha=ALPHA, rc=RC, K=K, order=ORDER).step(0)
+    assert e0["coulomb"] == pytest.approx(e_new["coulomb"], rel=1e-12)
+    sd.step(5)
+    x3, v3, _, _, _ = oracle_verlet(s, q, 3)
+    x_o, v_o, _, _, _ = oracle_verlet(dataclasses.replace(s, x=x3, v=v3), q2, 5)
+    st = c.state(forces=False)
+    assert np.linalg.norm(periodic_diff(st["x"], x_o, s.box)) <= 1e-9 * np.linalg.norm(x_o)
+    assert rel_l2(st["v"], v_o) <= 1e-9
+    sd.close()
+    c.close()
 
 
 @pytest.fixture(scope="module")
