@@ -261,12 +261,16 @@ md_status md_info(md_ctx *ctx, int32_t *nbox, int64_t *n_total);
  * It allocates nothing: its intermediates live in one fixed array inside the
  * library (about 4 MiB, held on every GPU that loads the library until the
  * process exits).  Limits: n <= 262144 and nc_x*nc_y*nc_z <= 131072, else
- * MD_ERR_ARG.  Host pointers are rejected (MD_ERR_ARG).  Errors are reported
+ * MD_ERR_ARG.  Cost: the per-cell ordering is O(m^2) for a cell of m atoms
+ * (one warp ranks each atom against the whole cell), so a cell holding
+ * thousands of atoms is slow; liquid densities put ~20 in a cell.  Host pointers are rejected (MD_ERR_ARG).  Errors are reported
  * through md_last_error(NULL).  The first call on a device looks up the
  * array's device address (a host-side query), so make that first call before
  * any stream capture.  All calls share the array: calls whose work may
  * overlap on the GPU (unordered streams) race and must be serialised by the
- * caller.  Positions must be finite. */
+ * caller.  Positions must be finite: a non-finite coordinate is clamped to
+ * an edge cell (no access leaves the arrays) but its place in the order is
+ * meaningless. */
 md_status md_bin_sort_noalloc(const md_box *box, int64_t n, const double *x, double rs,
                               int32_t *perm, void *stream);
 

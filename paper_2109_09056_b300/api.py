@@ -278,7 +278,22 @@ def md_debug_expire_waits(ctx: Ctx, on: bool = True) -> None:
 
 def md_bin_sort_noalloc(box, x, rs: float, perm, stream=None) -> None:
     """Binning + stable cell-order permutation into the caller's device array
-    `perm` without any device allocation (x and perm must be CUDA tensors)."""
+    `perm` without any device allocation.  x must be a contiguous CUDA float64
+    tensor of shape (n, 3) and perm a contiguous CUDA int32 tensor with at
+    least n elements on the same device; nothing is converted (a converted copy
+    would leave the caller's perm unwritten), anything else raises MDError."""
+    def bad(msg):
+        raise N.MDError(N.MD_ERR_ARG, "md_bin_sort_noalloc: " + msg)
+    if not (_is_torch(x) and _is_torch(perm)):
+        bad("x and perm must be torch tensors")
+    if not (x.is_cuda and perm.is_cuda):
+        bad("x and perm must be CUDA tensors")
+    if x.device != perm.device:
+        bad("x and perm must be on the same device")
+    if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_contiguous():
+        bad("x must be a contiguous float64 tensor of shape (n, 3)")
+    if perm.dtype != torch.int32 or not perm.is_contiguous() or perm.numel() < x.shape[0]:
+        bad("perm must be a contiguous int32 tensor with at least n elements")
     b = N.md_box()
     for d in range(3):
         b.L[d] = float(box[d])

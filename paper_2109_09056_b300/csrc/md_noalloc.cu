@@ -11,10 +11,13 @@
 // library, until the process exits).
 //
 // Limits: at most kMaxAtoms atoms and kMaxCells cells; larger requests are
-// rejected with MD_ERR_ARG.  The array is shared by every call on a device and
-// keeps the previous call's contents; the histogram part is cleared at the
-// start of each call.  Two calls whose work overlaps on the GPU (different
-// streams without ordering) race on the array.
+// rejected with MD_ERR_ARG.  The per-cell ordering ranks each atom against
+// every atom of its cell (one warp per cell), so a cell of m atoms costs
+// O(m^2) work: fine at liquid densities (~20 per cell), slow for a dense
+// cluster of thousands of atoms in one cell.  The array is shared by every
+// call on a device and keeps the previous call's contents; the histogram part
+// is cleared at the start of each call.  Two calls whose work overlaps on the
+// GPU (different streams without ordering) race on the array.
 #include <cmath>
 #include <mutex>
 
@@ -162,8 +165,12 @@ extern "C" md_status md_bin_sort_noalloc(const md_box *box, int64_t n, const dou
         const double L = box->L[d];
         if (!std::isfinite(L) || !(L > 2.0 * rs))
             return set_global_error(MD_ERR_BOX_TOO_SMALL, "md_bin_sort_noalloc: box edge must exceed 2*rs");
+        // checked in FP64 before the conversion: a huge L/rs must not wrap
+        const double ncd = std::floor(L / rs);
+        if (!(ncd <= (double)kMaxCells))
+            return set_global_error(MD_ERR_ARG, "md_bin_sort_noalloc: more than 131072 cells");
         g.L[d] = L;
-        g.nc[d] = (int32_t)std::floor(L / rs);
+        g.nc[d] = (int32_t)ncd;
         g.inv[d] = (double)g.nc[d] / L;
         ncell *= g.nc[d];
     }
