@@ -69,6 +69,15 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float t) {
     s = u;
 }
 
+// 1/x by the hardware's approximate reciprocal (one instruction, within about
+// an ulp; denormal results flush to zero), where __fdividef(1, x) adds a range
+// check and a multiply (B300, 4M atoms: 0.697 -> 0.666 ms per force launch).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int T>
 __device__ __forceinline__ double sum_lanes_d(double x) {
 #pragma unroll
@@ -551,7 +560,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
             const float dz = (sj.z + s_off[wib][2][cd]) - si.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const bool in = r2 < rc2f;
-            const float r2inv = __fdividef(1.0f, r2);
+            const float r2inv = rcp_approx(r2);
             float s2, e4, ush, w;
             if (ONE) {
                 s2 = s2_0; e4 = e4_0; ush = ush_0;
