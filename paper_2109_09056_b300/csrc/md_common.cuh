@@ -277,8 +277,10 @@ cudaError_t launch_get_neighbors(md_ctx *c, int32_t *nn_out, int32_t *nbr_out, i
 cudaError_t launch_adjoint(md_ctx *c, const double *G_aos, double gE, double *dx_aos,
                            double *totals_out, double *scratch);
 size_t adjoint_scratch_doubles(md_ctx *c);
-// The list entry that pads rows: the dummy shadow slot ns (kept far from every
-// atom) with a zero offset; a pair evaluated against it is masked by rc.
+// The list entry that pads rows past their count (up to the warp-tile's
+// longest row after each build; the rows of padding slots hold it from the
+// list's allocation on): the dummy shadow slot ns (kept far from every atom)
+// with a zero offset; a pair evaluated against it is masked by rc.
 __host__ __device__ inline uint32_t sentinel_entry(int64_t ns) {
     return (uint32_t)ns | (kCodeZero << MD_IDX_BITS);
 }

@@ -457,22 +457,138 @@ __device__ __forceinline__ int tile_rows(int ni) {
     return __reduce_max_sync(0xffffffffu, (ni + T - 1) / T);
 }
 
+// Loop-invariant pair constants of the mixed kernels.
+struct MixedConst {
+    int nt;
+    float rc2f, c1_0, c1x2_0, s2_0, e4_0, ush_0;
+};
+
+__device__ __forceinline__ MixedConst mixed_const(const ForceArgs &a, const SmemTabs &tb) {
+    MixedConst k;
+    k.nt = a.pair->nt;
+    k.rc2f = a.pair->rc2f;
+    k.c1_0 = tb.fc1[0];
+    k.c1x2_0 = 2.0f * k.c1_0;
+    k.s2_0 = tb.fs2[0];
+    k.e4_0 = tb.fe4[0];
+    k.ush_0 = tb.fush[0];
+    return k;
+}
+
+// One lane's Kahan-compensated FP32 partial sums (value = s - c).
+struct Acc {
+    float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
+};
+
+// The pair terms of one lane's share of a list block: rows [0, rows) of the
+// block in shared memory (Lr: this lane's word of row 0, rows 32 words apart;
+// a row's slots past its atom's count hold the sentinel entry up to the
+// block's longest row), for the home atom with shadow si and type ti.  off:
+// the warp's stencil offsets (off[d][code]).
+template <bool ONE, bool THERMO>
+__device__ __forceinline__ void lane_rows(const ForceArgs &a, const SmemTabs &tb,
+                                          const MixedConst &k, const float (*off)[32],
+                                          const uint32_t *Lr, int rows, const float4 &si, int ti,
+                                          Acc &acc) {
+    constexpr int G = MD_FORCE_GROUP;
+    static_assert(kBatch % G == 0, "MD_FORCE_GROUP must divide MD_FORCE_BATCH");
+    // One list entry: x_j - x_i from the shadows and the stencil offset,
+    // the LJ term masked at rc (sentinel entries past an atom's count sit
+    // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
+    auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
+                     float &tp) {
+        const unsigned cd = en >> MD_IDX_BITS;
+        const float dx = (sj.x + off[0][cd]) - si.x;
+        const float dy = (sj.y + off[1][cd]) - si.y;
+        const float dz = (sj.z + off[2][cd]) - si.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool in = r2 < k.rc2f;
+        const float r2inv = rcp_approx(r2);
+        float s2, e4, ush, w;
+        if (ONE) {
+            s2 = k.s2_0; e4 = k.e4_0; ush = k.ush_0;
+        } else {
+            const int ab = ti * k.nt + __float_as_int(sj.w);
+            s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
+        }
+        const float q2 = s2 * r2inv;
+        const float s6 = q2 * q2 * q2;
+        // phi = 24 eps / r^2 (sigma/r)^6 [2 (sigma/r)^6 - 1] = c1 q2 s6 (2 s6 - 1),
+        // c1 = 24 eps / sigma^2
+        if (ONE) w = fmaf(k.c1x2_0, s6, -k.c1_0);
+        else w = tb.fc1[ti * k.nt + __float_as_int(sj.w)] * fmaf(2.0f, s6, -1.0f);
+        const float phi = in ? (q2 * s6) * w : 0.0f;
+        tx = -phi * dx;
+        ty = -phi * dy;
+        tz = -phi * dz;
+        tp = (THERMO && in) ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f;
+    };
+    // groups of G consecutive terms are added by an FMA chain, each group
+    // sum into the lane's partial by one Kahan step
+    auto batch = [&](const uint32_t (&eb)[kBatch], const float4 (&sj)[kBatch]) {
+        float gx = 0.f, gy = 0.f, gz = 0.f, gp = 0.f;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            float tx, ty, tz, tp;
+            terms(eb[u], sj[u], tx, ty, tz, tp);
+            if (u % G == 0) {
+                gx = tx; gy = ty; gz = tz; gp = tp;
+            } else {
+                gx += tx; gy += ty; gz += tz; gp += tp;
+            }
+            if (u % G == G - 1) {
+                kahan_add(acc.fx, acc.cx, gx);
+                kahan_add(acc.fy, acc.cy, gy);
+                kahan_add(acc.fz, acc.cz, gz);
+                if (THERMO) kahan_add(acc.pe, acc.cp, gp);
+            }
+        }
+    };
+    // whole batches, then the remaining rows one at a time
+    const int rows_full = rows / kBatch * kBatch;
+    for (int q = 0; q < rows_full; q += kBatch) {
+        uint32_t eb[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) eb[u] = Lr[(q + u) * 32];
+        float4 sj[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            sj[u] = __ldg(a.sh_in + chk_index(eb[u] & MD_IDX_MASK, a.ns + 1, CHK_FORCE_GATHER,
+                                              a.fl, a.ns));
+        batch(eb, sj);
+    }
+    for (int q = rows_full; q < rows; ++q) {
+        const uint32_t en = Lr[q * 32];
+        const float4 sj = __ldg(a.sh_in + chk_index(en & MD_IDX_MASK, a.ns + 1,
+                                                    CHK_FORCE_GATHER, a.fl, a.ns));
+        float tx, ty, tz, tp;
+        terms(en, sj, tx, ty, tz, tp);
+        kahan_add(acc.fx, acc.cx, tx);
+        kahan_add(acc.fy, acc.cy, ty);
+        kahan_add(acc.fz, acc.cz, tz);
+        if (THERMO) kahan_add(acc.pe, acc.cp, tp);
+    }
+}
+
+// The warp's stencil offsets (code `lane`; codes 27..31 unused: zero) for box B.
+__device__ __forceinline__ void set_offsets(float (*off)[32], const Box &B, int lane) {
+    const bool code = lane < 27;
+    off[0][lane] = code ? (float)(lane % 3 - 1) * B.hf[0] : 0.f;
+    off[1][lane] = code ? (float)((lane / 3) % 3 - 1) * B.hf[1] : 0.f;
+    off[2][lane] = code ? (float)(lane / 9 - 1) * B.hf[2] : 0.f;
+}
+
 template <int T, bool ONE, bool THERMO>
 __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
                                            float (*s_off)[3][32], uint64_t (*s_bar)[2],
                                            uint32_t *lbuf) {
     constexpr int A = 32 / T;
-    constexpr int G = MD_FORCE_GROUP;
-    static_assert(kBatch % G == 0, "MD_FORCE_GROUP must divide MD_FORCE_BATCH");
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, sub = lane % T;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwc = blockDim.x >> 5;
     const int64_t chunk = (a.nwt + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * chunk;
     const int64_t t1 = min(a.nwt, t0 + chunk);
-    const int nt = a.pair->nt;
-    const float rc2f = a.pair->rc2f;
-    const float c1_0 = tb.fc1[0], s2_0 = tb.fs2[0], e4_0 = tb.fe4[0], ush_0 = tb.fush[0];
-    const float c1x2_0 = 2.0f * c1_0;
+    const MixedConst kc = mixed_const(a, tb);
     const size_t rowblk = (size_t)a.R * 32;  // words in one warp-tile's list block
     const uint64_t pol = l2_evict_first_policy();
     const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(lbuf + (size_t)wib * 2 * rowblk);
@@ -517,13 +633,8 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         const int b = b_next;
         if (has_next) b_next = a.tile_box[(wn * A) >> 5];
         if (b != curbox) {
-            // offset of stencil code `lane` (codes 27..31 unused: zero), and
-            // the box's slot range
             const Box &B = a.boxes[b];
-            const bool code = lane < 27;
-            s_off[wib][0][lane] = code ? (float)(lane % 3 - 1) * B.hf[0] : 0.f;
-            s_off[wib][1][lane] = code ? (float)((lane / 3) % 3 - 1) * B.hf[1] : 0.f;
-            s_off[wib][2][lane] = code ? (float)(lane / 9 - 1) * B.hf[2] : 0.f;
+            set_offsets(s_off[wib], B, lane);
             box_slot = B.slot_off;
             box_n = B.n;
             curbox = b;
@@ -547,93 +658,185 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         }
         phase ^= 1u << cb;
         __syncwarp();  // s_off is visible to the whole warp
-        const uint32_t *Lr = lbuf + (size_t)wib * 2 * rowblk + cb * rowblk + lane;
-        float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pe = 0.f, cp = 0.f;
-        // One list entry: x_j - x_i from the shadows and the stencil offset,
-        // the LJ term masked at rc (sentinel entries past an atom's count sit
-        // far beyond it): t = -phi (x_j - x_i), tp = the pair energy half.
-        auto terms = [&](const uint32_t en, const float4 &sj, float &tx, float &ty, float &tz,
-                         float &tp) {
-            const unsigned cd = en >> MD_IDX_BITS;
-            const float dx = (sj.x + s_off[wib][0][cd]) - si.x;
-            const float dy = (sj.y + s_off[wib][1][cd]) - si.y;
-            const float dz = (sj.z + s_off[wib][2][cd]) - si.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool in = r2 < rc2f;
-            const float r2inv = rcp_approx(r2);
-            float s2, e4, ush, w;
-            if (ONE) {
-                s2 = s2_0; e4 = e4_0; ush = ush_0;
-            } else {
-                const int ab = ti * nt + __float_as_int(sj.w);
-                s2 = tb.fs2[ab]; e4 = tb.fe4[ab]; ush = tb.fush[ab];
-            }
-            const float q2 = s2 * r2inv;
-            const float s6 = q2 * q2 * q2;
-            // phi = 24 eps / r^2 (sigma/r)^6 [2 (sigma/r)^6 - 1] = c1 q2 s6 (2 s6 - 1),
-            // c1 = 24 eps / sigma^2
-            if (ONE) w = fmaf(c1x2_0, s6, -c1_0);
-            else w = tb.fc1[ti * nt + __float_as_int(sj.w)] * fmaf(2.0f, s6, -1.0f);
-            const float phi = in ? (q2 * s6) * w : 0.0f;
-            tx = -phi * dx;
-            ty = -phi * dy;
-            tz = -phi * dz;
-            tp = (THERMO && in) ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f;
-        };
-        // groups of G consecutive terms are added by an FMA chain, each group
-        // sum into the lane's partial by one Kahan step
-        auto batch = [&](const uint32_t (&eb)[kBatch], const float4 (&sj)[kBatch]) {
-            float gx = 0.f, gy = 0.f, gz = 0.f, gp = 0.f;
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                float tx, ty, tz, tp;
-                terms(eb[u], sj[u], tx, ty, tz, tp);
-                if (u % G == 0) {
-                    gx = tx; gy = ty; gz = tz; gp = tp;
-                } else {
-                    gx += tx; gy += ty; gz += tz; gp += tp;
-                }
-                if (u % G == G - 1) {
-                    kahan_add(fx, cx, gx);
-                    kahan_add(fy, cy, gy);
-                    kahan_add(fz, cz, gz);
-                    if (THERMO) kahan_add(pe, cp, gp);
-                }
-            }
-        };
-        // whole batches, then the remaining rows one at a time
-        const int rows_full = rows_cur / kBatch * kBatch;
-        for (int q = 0; q < rows_full; q += kBatch) {
-            uint32_t eb[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) eb[u] = Lr[(q + u) * 32];
-            float4 sj[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                sj[u] = __ldg(a.sh_in + chk_index(eb[u] & MD_IDX_MASK, a.ns + 1, CHK_FORCE_GATHER,
-                                                  a.fl, a.ns));
-            batch(eb, sj);
-        }
-        for (int q = rows_full; q < rows_cur; ++q) {
-            const uint32_t en = Lr[q * 32];
-            const float4 sj = __ldg(a.sh_in + chk_index(en & MD_IDX_MASK, a.ns + 1,
-                                                        CHK_FORCE_GATHER, a.fl, a.ns));
-            float tx, ty, tz, tp;
-            terms(en, sj, tx, ty, tz, tp);
-            kahan_add(fx, cx, tx);
-            kahan_add(fy, cy, ty);
-            kahan_add(fz, cz, tz);
-            if (THERMO) kahan_add(pe, cp, tp);
-        }
+        Acc acc;
+        lane_rows<ONE, THERMO>(a, tb, kc, s_off[wib],
+                               lbuf + (size_t)wib * 2 * rowblk + cb * rowblk + lane, rows_cur, si,
+                               ti, acc);
         __syncwarp();  // done reading this half; the next copy may refill it
         // each lane folds its compensation (value = s - c); the T lane
         // partials of an atom are then added in a fixed xor-shuffle order
-        const float Ff[3] = {sum_lanes_f<T>(fx - cx), sum_lanes_f<T>(fy - cy),
-                             sum_lanes_f<T>(fz - cz)};
-        const double ped = THERMO ? (double)sum_lanes_f<T>(pe - cp) : 0.0;
+        const float Ff[3] = {sum_lanes_f<T>(acc.fx - acc.cx), sum_lanes_f<T>(acc.fy - acc.cy),
+                             sum_lanes_f<T>(acc.fz - acc.cz)};
+        const double ped = THERMO ? (double)sum_lanes_f<T>(acc.pe - acc.cp) : 0.0;
         finish_tile<T, THERMO, kPre>(a, tb, wt, i, valid, ti, Ff, ped, st);
         cb ^= 1;
         rows_cur = rows_next;
+    }
+}
+
+// Rows [0, r0) and [0, r1) of two list blocks (128 bytes a row) -> shared
+// dst0 and dst1 as two bulk copies completing on one mbarrier (one arrival
+// posting both byte counts).  One lane only.
+__device__ __forceinline__ void bulk_rows2(uint32_t dst0, const uint32_t *src0, int r0,
+                                           uint32_t dst1, const uint32_t *src1, int r1,
+                                           uint32_t bar, uint64_t pol, uint32_t extra) {
+    const uint32_t b0 = (uint32_t)r0 * 128u, b1 = (uint32_t)r1 * 128u;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                 "r"(b0 + b1 + extra)
+                 : "memory");
+    if (b0 > 0)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+            "[%0], [%1], %2, [%3], %4;\n" ::"r"(dst0),
+            "l"(src0), "r"(b0), "r"(bar), "l"(pol)
+            : "memory");
+    if (b1 > 0)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+            "[%0], [%1], %2, [%3], %4;\n" ::"r"(dst1),
+            "l"(src1), "r"(b1), "r"(bar), "l"(pol)
+            : "memory");
+}
+
+// Eight lanes per atom on the 8-lane list layout (4 atoms per list block),
+// walked in tiles of 8 atoms: the two blocks of a tile arrive by one pair of
+// bulk copies, then the 8 lanes of each group take atom g of the first block
+// and, in a second pass, atom 4 + g of the second.  One gather instruction
+// then covers 4 atoms x 8 consecutive list entries instead of 8 atoms x 4: a
+// quarter-warp (8 lanes) reads one atom's run of neighbors, which touches
+// fewer distinct 128-byte lines.  The epilogue runs once per 8 atoms with 4
+// lanes per atom (as the 4-lane traversal), the forces moved there by shuffles.
+template <bool ONE, bool THERMO>
+__device__ __forceinline__ void mixed_body_pairs(const ForceArgs &a, const SmemTabs &tb,
+                                                 float (*s_off)[3][32], uint64_t (*s_bar)[2],
+                                                 uint32_t *lbuf) {
+    constexpr int T = 8, A = 4;  // the list layout
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, g = lane >> 3;
+    const int nwc = blockDim.x >> 5;
+    const int64_t nst = a.nwt / 2;  // tiles of 8 atoms (block pairs)
+    const int64_t chunk = (nst + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * chunk;
+    const int64_t t1 = min(nst, t0 + chunk);
+    const MixedConst kc = mixed_const(a, tb);
+    const size_t rowblk = (size_t)a.R * 32;  // words in one list block
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t *wbuf = lbuf + (size_t)wib * 4 * rowblk;  // 2 halves x 2 blocks
+    const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(wbuf);
+    const uint32_t bbytes = (uint32_t)(rowblk * 4);  // bytes per block
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[wib][0]);
+    uint32_t phase = 0;
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    auto issue = [&](int64_t st, int half, int r0, int r1) {
+        if (lane == 0)
+            bulk_rows2(sbuf0 + (uint32_t)half * 2u * bbytes, a.nbr + (2 * st) * rowblk, r0,
+                       sbuf0 + (uint32_t)half * 2u * bbytes + bbytes, a.nbr + (2 * st + 1) * rowblk,
+                       r1, bar0 + 8 * half, pol, a.tx_extra);
+    };
+    int64_t st = t0 + wib;
+    int rows0 = 0, rows1 = 0;
+    int nn0_next = 0, nn1_next = 0;
+    float4 s0_next = make_float4(0.f, 0.f, 0.f, 0.f), s1_next = s0_next;
+    int b_next = 0;
+    int64_t box_slot = 0;
+    int32_t box_n = 0;
+    if (st < t1) {
+        b_next = a.tile_box[(st * 8) >> 5];
+        rows0 = tile_rows<T>(min(__ldg(a.nn + st * 8 + g), a.pad));
+        rows1 = tile_rows<T>(min(__ldg(a.nn + st * 8 + 4 + g), a.pad));
+        issue(st, 0, rows0, rows1);
+        if (st + nwc < t1) {
+            nn0_next = __ldg(a.nn + (st + nwc) * 8 + g);
+            nn1_next = __ldg(a.nn + (st + nwc) * 8 + 4 + g);
+        }
+        s0_next = a.sh_in[st * 8 + g];
+        s1_next = a.sh_in[st * 8 + 4 + g];
+    }
+    int cb = 0;
+    int curbox = -1;
+    for (; st < t1; st += nwc) {
+        const int64_t sn = st + nwc;
+        const bool has_next = sn < t1;
+        int r0n = 0, r1n = 0;
+        if (has_next) {
+            r0n = tile_rows<T>(min(nn0_next, a.pad));
+            r1n = tile_rows<T>(min(nn1_next, a.pad));
+            issue(sn, cb ^ 1, r0n, r1n);
+        }
+        if (sn + nwc < t1) {
+            nn0_next = __ldg(a.nn + (sn + nwc) * 8 + g);
+            nn1_next = __ldg(a.nn + (sn + nwc) * 8 + 4 + g);
+        }
+        const int b = b_next;
+        if (has_next) b_next = a.tile_box[(sn * 8) >> 5];
+        if (b != curbox) {
+            const Box &B = a.boxes[b];
+            set_offsets(s_off[wib], B, lane);
+            box_slot = B.slot_off;
+            box_n = B.n;
+            curbox = b;
+        }
+        const float4 s0 = s0_next, s1 = s1_next;
+        if (has_next) {
+            s0_next = a.sh_in[sn * 8 + g];
+            s1_next = a.sh_in[sn * 8 + 4 + g];
+        }
+        const int ti0 = ONE ? 0 : __float_as_int(s0.w), ti1 = ONE ? 0 : __float_as_int(s1.w);
+        // the epilogue's atom: 4 lanes each, lane 4e + d takes component d
+        const int64_t ie = st * 8 + (lane >> 2);
+        const bool valid_e = (ie - box_slot) < box_n;
+        TileState<4> ts;
+        load_tile_state<4>(a, ie, valid_e, ts);
+        if (!mbar_wait(bar0 + 8 * cb, (phase >> cb) & 1u)) {
+            atomicOr(&a.fl->status, ST_TIMEOUT);
+            if (has_next) mbar_wait(bar0 + 8 * (cb ^ 1), (phase >> (cb ^ 1)) & 1u);
+            return;
+        }
+        phase ^= 1u << cb;
+        __syncwarp();
+        const uint32_t *Lb = wbuf + (size_t)cb * 2 * rowblk + lane;
+        Acc acc0, acc1;
+        lane_rows<ONE, THERMO>(a, tb, kc, s_off[wib], Lb, rows0, s0, ti0, acc0);
+        lane_rows<ONE, THERMO>(a, tb, kc, s_off[wib], Lb + rowblk, rows1, s1, ti1, acc1);
+        __syncwarp();  // done reading this half
+        const float F0[3] = {sum_lanes_f<T>(acc0.fx - acc0.cx), sum_lanes_f<T>(acc0.fy - acc0.cy),
+                             sum_lanes_f<T>(acc0.fz - acc0.cz)};
+        const float F1[3] = {sum_lanes_f<T>(acc1.fx - acc1.cx), sum_lanes_f<T>(acc1.fy - acc1.cy),
+                             sum_lanes_f<T>(acc1.fz - acc1.cz)};
+        // atom e = lane / 4 of the tile: group e of the first pass (e < 4) or
+        // group e - 4 of the second
+        const int src = 8 * ((lane >> 2) & 3);
+        const bool second = lane >= 16;
+        float Fe[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float u0 = __shfl_sync(0xffffffffu, F0[d], src);
+            const float u1 = __shfl_sync(0xffffffffu, F1[d], src);
+            Fe[d] = second ? u1 : u0;
+        }
+        double ped = 0.0;
+        if (THERMO) {
+            const float p0 = __shfl_sync(0xffffffffu, sum_lanes_f<T>(acc0.pe - acc0.cp), src);
+            const float p1 = __shfl_sync(0xffffffffu, sum_lanes_f<T>(acc1.pe - acc1.cp), src);
+            ped = (double)(second ? p1 : p0);
+        }
+        int te = 0;
+        if (!ONE) {
+            const int u0 = __shfl_sync(0xffffffffu, ti0, src), u1 = __shfl_sync(0xffffffffu, ti1, src);
+            te = second ? u1 : u0;
+        }
+        // thermo partials: the tile's in the slot of its first block, zero in
+        // the second's
+        finish_tile<4, THERMO, true>(a, tb, 2 * st, ie, valid_e, te, Fe, ped, ts);
+        if (THERMO && lane < TP) a.tpart[(2 * st + 1) * TP + lane] = 0.0;
+        cb ^= 1;
+        rows0 = r0n;
+        rows1 = r1n;
     }
 }
 
@@ -692,8 +895,13 @@ __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
     __syncthreads();
     const int64_t clock = a.fl->clock;
     const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
-    if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, s_bar, lbuf);
-    else mixed_body<T, ONE, false>(a, tb, s_off, s_bar, lbuf);
+    if constexpr (T == 8) {
+        if (thermo) mixed_body_pairs<ONE, true>(a, tb, s_off, s_bar, lbuf);
+        else mixed_body_pairs<ONE, false>(a, tb, s_off, s_bar, lbuf);
+    } else {
+        if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, s_bar, lbuf);
+        else mixed_body<T, ONE, false>(a, tb, s_off, s_bar, lbuf);
+    }
     kernel_done(a, clock, thermo);
 }
 
@@ -875,9 +1083,11 @@ int auto_block_mixed(const md_ctx *c, int64_t nwt, size_t per_warp_smem) {
 template <bool MIXED, int T, bool ONE>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if constexpr (MIXED) {
-        // Each warp has a double buffer of R list rows in shared memory.
-        const size_t per_warp = (size_t)2 * a.R * 32 * sizeof(uint32_t);
-        int block = c->block ? c->block : auto_block_mixed(c, a.nwt, per_warp);
+        // Each warp has a double buffer of R list rows in shared memory (of two
+        // list blocks with 8 lanes per atom).
+        const int64_t units = T == 8 ? a.nwt / 2 : a.nwt;  // tiles a warp takes in turn
+        const size_t per_warp = (size_t)(T == 8 ? 4 : 2) * a.R * 32 * sizeof(uint32_t);
+        int block = c->block ? c->block : auto_block_mixed(c, units, per_warp);
         // an explicit size is an upper bound: fewer warps when their buffers
         // would not fit in shared memory
         while (block > 32 && (size_t)(block / 32) * per_warp > kSmemDyn) block -= 32;
@@ -908,7 +1118,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
             per_sm = occ;
         }
         int64_t grid = (int64_t)c->nsm * per_sm;
-        const int64_t need = (a.nwt + warps - 1) / warps;
+        const int64_t need = (units + warps - 1) / warps;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);

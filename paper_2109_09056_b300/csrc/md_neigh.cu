@@ -9,10 +9,11 @@
 // (about a quarter of them).  It then takes the window 64 candidates at a
 // time: each lane holds two and tests them against every home atom (a
 // broadcast read), one ballot per home atom and candidate half, which lands in
-// that atom's lane as a 32-bit accept mask; each lane then writes its atom's
-// accepted candidates, in candidate order, into the atom's row of the
-// warp-transposed padded list, then the sentinel entry into the row's
-// remaining slots (the rows of padding slots hold it from the list's
+// that atom's lane as a 32-bit accept mask (through shared memory); each lane
+// then writes its atom's accepted candidates, in candidate order, into the
+// atom's row of the warp-transposed padded list.  A second kernel then writes
+// the sentinel entry into the slots past each atom's count up to its
+// warp-tile's longest row (the rows of padding slots hold it from the list's
 // allocation on).
 //
 // Decision rule (bit-exact with the FP64 definition): a pair is a neighbor iff
@@ -37,10 +38,13 @@ namespace mdb {
 namespace {
 
 constexpr int kWarps = 4;       // cells per CTA (one warp each)
-// Candidates staged per warp per window: small enough that eight 4-warp CTAs
-// fit in shared memory (B300, 4M atoms: 640 -> 3.18 ms per build, 384 -> 2.75
-// ms; a typical stencil then takes two windows).
-constexpr int kCand = 384;
+// Kept candidates staged per warp per window (a multiple of 64): a typical
+// stencil (~390 after the cull) fits one window.
+#ifndef MD_BUILD_CAND
+#define MD_BUILD_CAND 384
+#endif
+constexpr int kCand = MD_BUILD_CAND;
+static_assert(kCand % 64 == 0 && kCand >= 64, "windows are tested 64 candidates at a time");
 
 struct BuildArgs {
     const Box *boxes;
@@ -77,10 +81,10 @@ __device__ __forceinline__ bool exact_test(const BuildArgs &a, const Box &B, int
     return same_image && (r2 < a.rs2);
 }
 
-// Resident CTAs per SM the build's register budget is sized for (8: 64
-// registers, no spills; with kCand 384 the shared memory of 8 CTAs fits too).
+// Resident CTAs per SM the build's register budget is sized for (7: 72
+// registers, no spills; the shared memory of 7 CTAs fits with kCand 384).
 #ifndef MD_BUILD_MINB
-#define MD_BUILD_MINB 8
+#define MD_BUILD_MINB 7
 #endif
 
 template <int T>
@@ -88,9 +92,12 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
     constexpr int A = 32 / T;
     if (a.fl->status & ST_FREEZE) return;
     __shared__ __align__(16) float4 cand[kWarps][kCand];
-    __shared__ int64_t s_start[kWarps][27];
-    __shared__ int32_t s_pref[kWarps][28];
+    __shared__ int32_t s_start[kWarps][27];
+    __shared__ int32_t s_cnt[kWarps][27];
+    __shared__ __align__(16) float4 s_off[kWarps][27];
     __shared__ __align__(16) float4 hpos[kWarps][32];
+    __shared__ int32_t s_self[kWarps][32];
+    __shared__ __align__(16) uint4 s_mask[kWarps][32];  // home atom hh's accept masks
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * kWarps + w;
     if (c >= a.ncell) return;  // whole warp
@@ -99,27 +106,20 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
     const int hm = a.cstart[c + 1] - a.cstart[c];
     if (hm == 0) return;  // whole warp
     const int64_t h0 = base + a.cstart[c];
-    // stencil slots: first slot and count of each of the 27 cells
-    int cnt_s = 0;
+    // stencil slots: first slot, count and coordinate offset of each of the 27 cells
     if (lane < 27) {
         const int loc = c - B.cell_off;
         const int cx = loc % B.nc[0], cy = (loc / B.nc[0]) % B.nc[1], cz = loc / (B.nc[0] * B.nc[1]);
-        const int nx = (cx + lane % 3 - 1 + B.nc[0]) % B.nc[0];
-        const int ny = (cy + (lane / 3) % 3 - 1 + B.nc[1]) % B.nc[1];
-        const int nz = (cz + lane / 9 - 1 + B.nc[2]) % B.nc[2];
+        const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+        const int nx = (cx + ox + B.nc[0]) % B.nc[0];
+        const int ny = (cy + oy + B.nc[1]) % B.nc[1];
+        const int nz = (cz + oz + B.nc[2]) % B.nc[2];
         const int ncl = B.cell_off + (nz * B.nc[1] + ny) * B.nc[0] + nx;
-        s_start[w][lane] = base + a.cstart[ncl];
-        cnt_s = a.cstart[ncl + 1] - a.cstart[ncl];
+        s_start[w][lane] = (int32_t)(base + a.cstart[ncl]);
+        s_cnt[w][lane] = a.cstart[ncl + 1] - a.cstart[ncl];
+        s_off[w][lane] = make_float4((float)ox * B.hf[0], (float)oy * B.hf[1],
+                                     (float)oz * B.hf[2], 0.f);
     }
-    int incl = cnt_s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane < 27) s_pref[w][lane + 1] = incl;
-    if (lane == 0) s_pref[w][0] = 0;
-    const int M = __shfl_sync(0xffffffffu, incl, 26);
     __syncwarp();
 
     const float hi = a.rs2f + a.bandf, lo = a.rs2f - a.bandf;
@@ -137,15 +137,15 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
         const bool active = lane < nh;
         const int64_t i = chk_index(h0 + hb + (active ? lane : 0), a.ns, CHK_BUILD_HOME, a.fl,
                                     0);  // this lane's home atom
-        const uint32_t self_meta = (uint32_t)i | (kCodeZero << MD_IDX_BITS);
         const float4 si = a.sh[i];
         __syncwarp();
         hpos[w][lane] = si;
+        s_self[w][lane] = -1;  // window * kCand + position of home atom hb + lane
         // row of atom i: entry k at ((i / A) R + k / T) 32 + (i % A) T + k % T
         uint32_t *const rowp = a.nbr + ((size_t)(i / A) * a.R) * 32 + (i % A) * T;
         int cnt = 0;
         // this lane's accepted candidates among window slots [gb, gb + 32), in
-        // candidate order, into its atom's row (the atom itself skipped)
+        // candidate order, into its atom's row (its own atom already cleared)
         auto write_chunk = [&](int gb, unsigned m_hi, unsigned m_lo) {
             unsigned acc = m_lo, band = m_hi & ~m_lo;
             while (band) {  // rare: candidates near rs^2 take the exact FP64 decision
@@ -153,58 +153,66 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
                 band &= band - 1u;
                 const float4 p = cand[w][gb + k];
                 const uint32_t meta = __float_as_uint(p.w);
-                if (meta != self_meta &&
-                    exact_test(a, B, i, meta & MD_IDX_MASK, p.x - si.x, p.y - si.y, p.z - si.z))
+                if (exact_test(a, B, i, meta & MD_IDX_MASK, p.x - si.x, p.y - si.y, p.z - si.z))
                     acc |= 1u << k;
             }
             while (acc) {
                 const int k = __ffs(acc) - 1;
                 acc &= acc - 1u;
                 const uint32_t meta = __float_as_uint(cand[w][gb + k].w);
-                if (meta != self_meta) {
-                    const unsigned uc = (unsigned)cnt;
-                    if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = meta;
-                    ++cnt;
-                }
+                const unsigned uc = (unsigned)cnt;
+                if (cnt < a.pad) rowp[(uc / T) * 32u + uc % T] = meta;
+                ++cnt;
             }
         };
-        for (int w0 = 0; w0 < M; w0 += kCand) {
-            const int Mw = min(kCand, M - w0);
+        // The 27 slots are staged into windows of up to kCand kept candidates,
+        // 32 candidates of one slot at a time; one window holds a typical
+        // stencil after the cull.
+        int s = 0, g_off = 0, win = 0;
+        while (s < 27) {
             __syncwarp();
             int mc = 0;  // candidates of this window kept in cand[w]
-            for (int s = 0; s < 27; ++s) {
-                const int lo_s = max(s_pref[w][s], w0), hi_s = min(s_pref[w][s + 1], w0 + Mw);
-                const float ox = (float)(s % 3 - 1) * B.hf[0];
-                const float oy = (float)((s / 3) % 3 - 1) * B.hf[1];
-                const float oz = (float)(s / 9 - 1) * B.hf[2];
-                for (int gs = lo_s; gs < hi_s; gs += 32) {
-                    const int g = gs + lane;
-                    bool keep = false;
-                    float4 q = far;
-                    if (g < hi_s) {
-                        const int64_t j = chk_index(s_start[w][s] + (g - s_pref[w][s]), a.ns,
-                                                    CHK_BUILD_CAND, a.fl, 0);
-                        const float4 p = a.sh[j];
-                        q = make_float4(p.x + ox, p.y + oy, p.z + oz,
-                                        __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));
-                        const float ex = fmaxf(fabsf(q.x) - ex_h, 0.f);
-                        const float ey = fmaxf(fabsf(q.y) - ey_h, 0.f);
-                        const float ez = fmaxf(fabsf(q.z) - ez_h, 0.f);
-                        keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < cull2;
-                    }
-                    const unsigned bk = __ballot_sync(0xffffffffu, keep);
-                    if (keep) cand[w][mc + __popc(bk & below)] = q;
-                    mc += __popc(bk);
+            while (s < 27) {
+                const int cnt_s = s_cnt[w][s];
+                const int take = min(32, cnt_s - g_off);
+                if (mc + take > kCand) break;  // the window is full (uniform)
+                bool keep = false;
+                float4 q = far;
+                if (lane < take) {
+                    const int64_t j =
+                        chk_index(s_start[w][s] + g_off + lane, a.ns, CHK_BUILD_CAND, a.fl, 0);
+                    const float4 p = a.sh[j];
+                    const float4 o = s_off[w][s];
+                    q = make_float4(p.x + o.x, p.y + o.y, p.z + o.z,
+                                    __uint_as_float((uint32_t)j | ((uint32_t)s << MD_IDX_BITS)));
+                    const float ex = fmaxf(fabsf(q.x) - ex_h, 0.f);
+                    const float ey = fmaxf(fabsf(q.y) - ey_h, 0.f);
+                    const float ez = fmaxf(fabsf(q.z) - ez_h, 0.f);
+                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < cull2;
+                }
+                const unsigned bk = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int pos = mc + __popc(bk & below);
+                    cand[w][pos] = q;
+                    // a home atom of this batch: record where it sits
+                    const int hk = g_off + lane - hb;
+                    if (s == (int)kCodeZero && hk >= 0 && hk < nh) s_self[w][hk] = win * kCand + pos;
+                }
+                mc += __popc(bk);
+                g_off += take;
+                if (g_off >= cnt_s) {
+                    ++s;
+                    g_off = 0;
                 }
             }
             const int Mp = (mc + 63) & ~63;  // kCand is a multiple of 64
             for (int g = mc + lane; g < Mp; g += 32) cand[w][g] = far;
             __syncwarp();
+            const int self = s_self[w][lane] - win * kCand;  // in this window iff in [0, Mp)
             for (int g0 = 0; g0 < Mp; g0 += 64) {
                 // Test phase: lane = candidates g0 + lane and g0 + 32 + lane
                 // against every home atom; home atom hh's ballots land in lane hh.
                 const float4 c0 = cand[w][g0 + lane], c1 = cand[w][g0 + 32 + lane];
-                unsigned hi0 = 0u, lo0 = 0u, hi1 = 0u, lo1 = 0u;
                 for (int hh = 0; hh < nh; ++hh) {
                     const float4 h = hpos[w][hh];
                     const float dx0 = c0.x - h.x, dy0 = c0.y - h.y, dz0 = c0.z - h.z;
@@ -215,22 +223,24 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
                     const unsigned bl0 = __ballot_sync(0xffffffffu, r20 < lo);
                     const unsigned bh1 = __ballot_sync(0xffffffffu, r21 <= hi);
                     const unsigned bl1 = __ballot_sync(0xffffffffu, r21 < lo);
-                    if (lane == hh) {
-                        hi0 = bh0; lo0 = bl0; hi1 = bh1; lo1 = bl1;
-                    }
+                    if (lane == 0) s_mask[w][hh] = make_uint4(bh0, bl0, bh1, bl1);
                 }
+                __syncwarp();
                 if (!active) continue;
+                const uint4 m = s_mask[w][lane];
+                unsigned hi0 = m.x, lo0 = m.y, hi1 = m.z, lo1 = m.w;
+                // the atom itself (distance 0, in the window once) is no neighbor
+                const unsigned d0 = (unsigned)(self - g0), d1 = (unsigned)(self - g0 - 32);
+                if (d0 < 32u) { hi0 &= ~(1u << d0); lo0 &= ~(1u << d0); }
+                if (d1 < 32u) { hi1 &= ~(1u << d1); lo1 &= ~(1u << d1); }
                 write_chunk(g0, hi0, lo0);
                 write_chunk(g0 + 32, hi1, lo1);
             }
+            ++win;
         }
         if (active) {
             a.nn[i] = cnt;
             if (cnt > a.pad) atomicOr(&a.fl->status, ST_OVERFLOW);
-            // the row's slots past its count hold the sentinel entry
-            const uint32_t sent = sentinel_entry(a.ns);
-            for (unsigned k = (unsigned)cnt; k < (unsigned)a.pad; ++k)
-                rowp[(k / T) * 32u + k % T] = sent;
         }
         const int mx = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
         const unsigned sm = __reduce_add_sync(0xffffffffu, active ? (unsigned)cnt : 0u);
@@ -239,6 +249,27 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
             atomicAdd(&a.fl->sumnn, (unsigned long long)sm);
         }
     }
+}
+
+// After a build: in each warp-tile (A atoms, T lanes each), the slots of rows
+// up to the tile's longest row that lie past their atom's count get the
+// sentinel entry, one coalesced row store at a time, so that the force kernel
+// can take whole rows up to the longest (rows past it are never read).
+template <int T>
+__global__ void __launch_bounds__(256) k_fill_tails(const int32_t *__restrict__ nn,
+                                                   uint32_t *__restrict__ nbr, int64_t nwt, int R,
+                                                   int pad, uint32_t sent, const Flags *fl) {
+    constexpr int A = 32 / T;
+    if (fl->status & ST_FREEZE) return;
+    const int64_t wt = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wt >= nwt) return;  // whole warp
+    const int lane = threadIdx.x & 31, sub = lane % T;
+    const int ni = min(__ldg(nn + wt * A + lane / T), pad);
+    const int nq = ni > sub ? (ni - sub + T - 1) / T : 0;  // this lane's entries
+    const int r0 = __reduce_min_sync(0xffffffffu, nq), r1 = __reduce_max_sync(0xffffffffu, nq);
+    uint32_t *row = nbr + (size_t)wt * R * 32 + lane;
+    for (int q = r0; q < r1; ++q)
+        if (q >= nq) row[(size_t)q * 32] = sent;
 }
 
 __global__ void k_fill_u32(uint32_t *__restrict__ p, size_t n, uint32_t v) {
@@ -251,14 +282,17 @@ template <int T>
 cudaError_t launch_build_t(md_ctx *c, const BuildArgs &a) {
     const unsigned grid = (unsigned)((c->ncell_tot + kWarps - 1) / kWarps);
     k_build<T><<<grid, kWarps * 32, 0, c->stream>>>(a);
+    const int64_t nwt = c->ns / (32 / T);
+    k_fill_tails<T><<<(unsigned)((nwt * 32 + 255) / 256), 256, 0, c->stream>>>(
+        c->nn, c->nbr, nwt, c->R, c->pad, sentinel_entry(c), c->dflags);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 // At allocation every list slot gets the sentinel entry; the rows of padding
-// slots keep it (no build writes them), every build rewrites the rows of real
-// atoms in full.
+// slots keep it (no build writes them); a build writes each real atom's
+// entries, then k_fill_tails the sentinels its warp-tile's readers need.
 cudaError_t fill_list_sentinel(md_ctx *c) {
     const size_t words = (size_t)c->ns * c->pad;
     k_fill_u32<<<(unsigned)std::min<size_t>((words + 255) / 256, 65535), 256, 0, c->stream>>>(
@@ -294,7 +328,7 @@ cudaError_t launch_build(md_ctx *c) {
         case 8: e = launch_build_t<8>(c, a); break;
         default: return cudaErrorInvalidValue;
     }
-    c->kernels += 1;
+    c->kernels += 2;
     return e;
 }
 

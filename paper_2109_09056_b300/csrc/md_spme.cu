@@ -637,14 +637,15 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
             float pl = 0.f, cl = 0.f;
             // kRealBatch entries per lane at a time: their list words, then
             // their shadows and charges, are all in flight before the math.
-            // Whole batches: the list pad is a multiple of kRealBatch x T and
-            // a row's entries past its count are sentinels, whose slot ns is
-            // far from every atom with no charge.
+            // Whole batches: a lane's entries past its count are replaced by
+            // the sentinel, whose slot ns is far from every atom, uncharged.
             const int nqr = (nq + kRealBatch - 1) & ~(kRealBatch - 1);
+            const uint32_t sent = sentinel_entry(a.ns);
             for (int k0 = 0; k0 < nqr; k0 += kRealBatch) {
                 uint32_t e[kRealBatch];
 #pragma unroll
-                for (int u = 0; u < kRealBatch; ++u) e[u] = __ldg(row + (size_t)(k0 + u) * 32);
+                for (int u = 0; u < kRealBatch; ++u)
+                    e[u] = k0 + u < nq ? __ldg(row + (size_t)(k0 + u) * 32) : sent;
                 float4 sj[kRealBatch];
                 float qj[kRealBatch];
                 int tj[kRealBatch];
