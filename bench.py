@@ -297,18 +297,22 @@ def spme_leg(args, stream, hbm_peak):
 def variants_leg(sysd, stream, hbm_peak):
     """Traversal / list-layout variants of the LJ step on the benchmark
     workload: the team size of the hierarchical traversal (lanes per atom,
-    which also fixes the list's warp-transposed layout) at 1, 2, 4 and 8.  Per
-    variant: the force kernel's device ms per launch (profiled launches, CUDA
-    events), its HBM fraction over the algorithmic bytes, and the whole step's
-    throughput over two rebuild periods."""
+    which also fixes the list's warp-transposed layout) at 1, 2, 4 and 8, and
+    half lists (each pair once, reactions by atomics; 4 lanes).  Per variant:
+    the force evaluation's device ms per launch (profiled launches, CUDA
+    events; with half lists the force kernel and its epilogue kernel), its HBM
+    fraction over its own algorithmic bytes, and the whole step's throughput
+    over two rebuild periods."""
     import torch
 
     from paper_2109_09056_b300 import MDSystem
-    res = {"workload": "see config", "axis": "lanes_per_atom", "md_steps": 2 * MD_PER_STEP}
-    for lanes in (1, 2, 4, 8):
+    res = {"workload": "see config", "axis": "lanes_per_atom (half: 4 lanes, half lists)",
+           "md_steps": 2 * MD_PER_STEP}
+    for lanes in (1, 2, 4, 8, "half"):
         m = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", rc=sysd.rc,
                      skin=sysd.skin, dt=sysd.dt, rebuild_every=sysd.rebuild_every,
-                     lanes_per_atom=lanes, stream=stream)
+                     lanes_per_atom=4 if lanes == "half" else lanes, half_list=lanes == "half",
+                     stream=stream)
         m.step(MD_PER_STEP)
         m.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)

@@ -83,6 +83,12 @@ typedef struct {
                                     memory; the FP64 kernel uses at most 256); 0 = automatic
                                     (768 when the system has enough warp-tiles and it fits) */
     int32_t use_graphs;          /* 1: md_step replays one rebuild period as a CUDA graph */
+    int32_t half_list;           /* 1: half Verlet lists (Newton's third law: each pair once,
+                                    its reaction added to the partner by FP32 atomics); mixed
+                                    precision with 4 lanes per atom only (else MD_ERR_ARG);
+                                    forces are then reproducible to rounding, not bitwise;
+                                    md_force_backward and md_spme_create refuse such a
+                                    context.  0: full lists (default). */
 } md_params;
 
 /* Fills p with the classic LJ-melt settings: 1 type, eps = sigma = m = 1,

@@ -67,7 +67,7 @@ void free_all(md_ctx *c) {
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
     F(c->tpart); F(c->tbox); F(c->fpart); F(c->tlog); F(c->dscratch); F(c->stage);
-    F(c->restage); F(c->scan_part); F(c->ctab);
+    F(c->restage); F(c->scan_part); F(c->ctab); F(c->facc);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -296,6 +296,8 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     c->T = p.lanes_per_atom ? p.lanes_per_atom : 4;  // automatic: see below for FP64
     if (c->T != 1 && c->T != 2 && c->T != 4 && c->T != 8)
         return fail(c, MD_ERR_ARG, "lanes_per_atom must be 1, 2, 4 or 8");
+    if (p.half_list && (p.precision != MD_MIXED || c->T != 4))
+        return fail(c, MD_ERR_ARG, "half_list needs MD_MIXED and 4 lanes per atom");
     c->block = p.block_threads;  // 0: chosen per launch (md_force.cu)
     if (c->block != 0 && (c->block < 64 || c->block > 768 || c->block % 32))
         return fail(c, MD_ERR_ARG, "block_threads must be 0 or 64..768, a multiple of 32");
@@ -368,6 +370,10 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     }
     CK(dalloc(&c->f, 3 * ns));
     CK(cudaMemset(c->f, 0, 3 * ns * sizeof(double)));
+    if (p.half_list) {  // kept at zero between force evaluations
+        CK(dalloc(&c->facc, ns + 1));
+        CK(cudaMemset(c->facc, 0, (ns + 1) * sizeof(float4)));
+    }
     CK(dalloc(&c->rbuild, 3 * ns));
     CK(dalloc(&c->xw, 3 * ns));
     CK(dalloc(&c->xws, 3 * ns));
@@ -427,7 +433,7 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     // list pad: observed rows in an LJ liquid stay within ~1.3x the mean count
     int pad = p.neigh_pad;
     if (pad <= 0) {
-        const double mean = 4.18879020478639 * rs * rs * rs * max_rho;
+        const double mean = 4.18879020478639 * rs * rs * rs * max_rho * (p.half_list ? 0.5 : 1.0);
         pad = (int)(1.15 * mean) + 8;
     }
     return alloc_list(c, pad);
@@ -947,6 +953,7 @@ md_status md_force_backward(md_ctx *c, const double *dL_dF, double dL_dE, double
     MD_TRACE("md_force_backward");
     if (!c || !dL_dF) return MD_ERR_ARG;
     if (c->hpair.nt > 4) return fail(c, MD_ERR_ARG, "md_force_backward supports ntypes <= 4");
+    if (c->params.half_list) return fail(c, MD_ERR_ARG, "md_force_backward needs full lists");
     if (!c->ready) return fail(c, MD_ERR_ARG, "internal: state between half-steps");
     // The list is recomputed from the current positions, never reused.
     CK(launch_bin_sort(c, false));

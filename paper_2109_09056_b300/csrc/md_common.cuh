@@ -212,6 +212,7 @@ struct md_ctx {
     int fsplit = 1;                // CTAs per box in the first thermo level
     double *tlog = nullptr;        // log rows * 4
     int32_t tlog_cap = 0;
+    float4 *facc = nullptr;        // half lists: per-slot force + energy accumulators (ns + 1)
     double *dscratch = nullptr;    // adjoint partials etc.
     size_t dscratch_bytes = 0;
     // pinned host mirrors

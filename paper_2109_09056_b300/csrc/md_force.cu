@@ -60,7 +60,15 @@ struct ForceArgs {
     int thermo_every;
     unsigned int *done;
     uint32_t tx_extra;  // test hook: list-copy bytes that never arrive (0 normally)
+    float4 *facc;       // half lists: force (x, y, z) and energy accumulators per slot
 };
+
+// Half lists: add (x, y, z, e) to slot j's accumulator (one vector reduction).
+__device__ __forceinline__ void red_add4(float4 *p, float x, float y, float z, float e) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z),
+                 "f"(e)
+                 : "memory");
+}
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float t) {
     const float y = t - c;
@@ -484,8 +492,10 @@ struct Acc {
 // block in shared memory (Lr: this lane's word of row 0, rows 32 words apart;
 // a row's slots past its atom's count hold the sentinel entry up to the
 // block's longest row), for the home atom with shadow si and type ti.  off:
-// the warp's stencil offsets (off[d][code]).
-template <bool ONE, bool THERMO>
+// the warp's stencil offsets (off[d][code]).  HALF: each entry is a pair
+// listed once; its reaction (and half its energy) goes to the partner's
+// accumulator.
+template <bool ONE, bool THERMO, bool HALF>
 __device__ __forceinline__ void lane_rows(const ForceArgs &a, const SmemTabs &tb,
                                           const MixedConst &k, const float (*off)[32],
                                           const uint32_t *Lr, int rows, const float4 &si, int ti,
@@ -522,6 +532,7 @@ __device__ __forceinline__ void lane_rows(const ForceArgs &a, const SmemTabs &tb
         ty = -phi * dy;
         tz = -phi * dz;
         tp = (THERMO && in) ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f;
+        if (HALF && in) red_add4(a.facc + (en & MD_IDX_MASK), -tx, -ty, -tz, tp);
     };
     // groups of G consecutive terms are added by an FMA chain, each group
     // sum into the lane's partial by one Kahan step
@@ -578,7 +589,7 @@ __device__ __forceinline__ void set_offsets(float (*off)[32], const Box &B, int 
     off[2][lane] = code ? (float)(lane / 9 - 1) * B.hf[2] : 0.f;
 }
 
-template <int T, bool ONE, bool THERMO>
+template <int T, bool ONE, bool THERMO, bool HALF>
 __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
                                            float (*s_off)[3][32], uint64_t (*s_bar)[2],
                                            uint32_t *lbuf) {
@@ -644,8 +655,9 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         if (has_next) si_next = a.sh_in[wn * A + lane / T];
         const int ti = ONE ? 0 : __float_as_int(si.w);
         // one lane per atom holds three components: there the registers are
-        // worth more to the rows (long ones) than the early loads
-        constexpr bool kPre = T >= 2;
+        // worth more to the rows (long ones) than the early loads (half lists:
+        // the epilogue is another kernel's)
+        constexpr bool kPre = T >= 2 && !HALF;
         TileState<T> st;
         if (kPre) load_tile_state<T>(a, i, valid, st);
         // the current tile's rows have landed; a wait that runs out abandons
@@ -659,7 +671,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         phase ^= 1u << cb;
         __syncwarp();  // s_off is visible to the whole warp
         Acc acc;
-        lane_rows<ONE, THERMO>(a, tb, kc, s_off[wib],
+        lane_rows<ONE, THERMO, HALF>(a, tb, kc, s_off[wib],
                                lbuf + (size_t)wib * 2 * rowblk + cb * rowblk + lane, rows_cur, si,
                                ti, acc);
         __syncwarp();  // done reading this half; the next copy may refill it
@@ -667,8 +679,14 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         // partials of an atom are then added in a fixed xor-shuffle order
         const float Ff[3] = {sum_lanes_f<T>(acc.fx - acc.cx), sum_lanes_f<T>(acc.fy - acc.cy),
                              sum_lanes_f<T>(acc.fz - acc.cz)};
-        const double ped = THERMO ? (double)sum_lanes_f<T>(acc.pe - acc.cp) : 0.0;
-        finish_tile<T, THERMO, kPre>(a, tb, wt, i, valid, ti, Ff, ped, st);
+        if (HALF) {
+            // the atom's own sums join the reactions in its accumulator
+            const float pf = THERMO ? sum_lanes_f<T>(acc.pe - acc.cp) : 0.0f;
+            if (valid && lane % T == 0) red_add4(a.facc + i, Ff[0], Ff[1], Ff[2], pf);
+        } else {
+            const double ped = THERMO ? (double)sum_lanes_f<T>(acc.pe - acc.cp) : 0.0;
+            finish_tile<T, THERMO, kPre>(a, tb, wt, i, valid, ti, Ff, ped, st);
+        }
         cb ^= 1;
         rows_cur = rows_next;
     }
@@ -711,7 +729,7 @@ template <bool ONE, bool THERMO>
 __device__ __forceinline__ void mixed_body_pairs(const ForceArgs &a, const SmemTabs &tb,
                                                  float (*s_off)[3][32], uint64_t (*s_bar)[2],
                                                  uint32_t *lbuf) {
-    constexpr int T = 8, A = 4;  // the list layout
+    constexpr int T = 8;  // the list layout (4 atoms per block)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, g = lane >> 3;
     const int nwc = blockDim.x >> 5;
     const int64_t nst = a.nwt / 2;  // tiles of 8 atoms (block pairs)
@@ -801,8 +819,8 @@ __device__ __forceinline__ void mixed_body_pairs(const ForceArgs &a, const SmemT
         __syncwarp();
         const uint32_t *Lb = wbuf + (size_t)cb * 2 * rowblk + lane;
         Acc acc0, acc1;
-        lane_rows<ONE, THERMO>(a, tb, kc, s_off[wib], Lb, rows0, s0, ti0, acc0);
-        lane_rows<ONE, THERMO>(a, tb, kc, s_off[wib], Lb + rowblk, rows1, s1, ti1, acc1);
+        lane_rows<ONE, THERMO, false>(a, tb, kc, s_off[wib], Lb, rows0, s0, ti0, acc0);
+        lane_rows<ONE, THERMO, false>(a, tb, kc, s_off[wib], Lb + rowblk, rows1, s1, ti1, acc1);
         __syncwarp();  // done reading this half
         const float F0[3] = {sum_lanes_f<T>(acc0.fx - acc0.cx), sum_lanes_f<T>(acc0.fy - acc0.cy),
                              sum_lanes_f<T>(acc0.fz - acc0.cz)};
@@ -881,10 +899,10 @@ __device__ __forceinline__ void kernel_done(const ForceArgs &a, int64_t clock, b
 #define MD_FORCE_MAXREG (65536 / (MD_FORCE_MINB * 128) / 8 * 8)
 static_assert(MD_FORCE_MAXREG * kMaxWarpsMixed * 32 <= 65536, "a full-size CTA must fit the SM");
 
-template <int T, bool ONE>
+template <int T, bool ONE, bool HALF>
 __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
-        mirror_state(a);
+        if (!HALF) mirror_state(a);  // half lists: the epilogue kernel mirrors
         return;
     }
     extern __shared__ __align__(128) uint32_t lbuf[];
@@ -899,8 +917,43 @@ __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
         if (thermo) mixed_body_pairs<ONE, true>(a, tb, s_off, s_bar, lbuf);
         else mixed_body_pairs<ONE, false>(a, tb, s_off, s_bar, lbuf);
     } else {
-        if (thermo) mixed_body<T, ONE, true>(a, tb, s_off, s_bar, lbuf);
-        else mixed_body<T, ONE, false>(a, tb, s_off, s_bar, lbuf);
+        if (thermo) mixed_body<T, ONE, true, HALF>(a, tb, s_off, s_bar, lbuf);
+        else mixed_body<T, ONE, false, HALF>(a, tb, s_off, s_bar, lbuf);
+    }
+    if (!HALF) kernel_done(a, clock, thermo);
+}
+
+// Half lists, after k_force_mixed<4, ONE, true>: each slot's accumulator holds
+// its force and half-energy sums (own terms and the reactions of the atoms
+// that list it); the epilogue of the 4-lane traversal runs on them (warp-tiles
+// of 8 atoms, lane 4e + d takes component d of atom e) and the accumulators
+// are cleared for the next evaluation.
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_half_epilogue(ForceArgs a) {
+    if (a.fl->status & ST_FREEZE) {
+        mirror_state(a);
+        return;
+    }
+    __shared__ SmemTabs tb;
+    load_tabs(*a.pair, tb);
+    __syncthreads();
+    const int64_t clock = a.fl->clock;
+    const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wt < a.nwt;
+         wt += nw) {
+        const int64_t i = wt * 8 + (lane >> 2);
+        const Box &B = a.boxes[a.tile_box[(wt * 8) >> 5]];
+        const bool valid = (i - B.slot_off) < B.n;
+        const float4 fa = a.facc[i];
+        __syncwarp();
+        if ((lane & 3) == 0) a.facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ti = ONE ? 0 : a.type[i];
+        const float F[3] = {fa.x, fa.y, fa.z};
+        TileState<4> st;
+        if (thermo) finish_tile<4, true, false>(a, tb, wt, i, valid, ti, F, (double)fa.w, st);
+        else finish_tile<4, false, false>(a, tb, wt, i, valid, ti, F, 0.0, st);
     }
     kernel_done(a, clock, thermo);
 }
@@ -1080,7 +1133,7 @@ int auto_block_mixed(const md_ctx *c, int64_t nwt, size_t per_warp_smem) {
     return 64;
 }
 
-template <bool MIXED, int T, bool ONE>
+template <bool MIXED, int T, bool ONE, bool HALF = false>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if constexpr (MIXED) {
         // Each warp has a double buffer of R list rows in shared memory (of two
@@ -1102,14 +1155,14 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
             std::lock_guard<std::mutex> lock(mu);
             if (smem > smem_set) {
                 cudaError_t e = cudaFuncSetAttribute(
-                    k_force_mixed<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    k_force_mixed<T, ONE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 smem_set = smem;
             }
             if (occ_smem != smem || occ_block != block) {
                 int per = 0;
                 cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per, k_force_mixed<T, ONE>, block, smem);
+                    &per, k_force_mixed<T, ONE, HALF>, block, smem);
                 if (e != cudaSuccess) return e;
                 occ = per > 0 ? per : 1;
                 occ_smem = smem;
@@ -1121,7 +1174,12 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         const int64_t need = (units + warps - 1) / warps;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
-        k_force_mixed<T, ONE><<<(unsigned)grid, block, smem, c->stream>>>(a);
+        k_force_mixed<T, ONE, HALF><<<(unsigned)grid, block, smem, c->stream>>>(a);
+        if constexpr (HALF) {
+            const int64_t blocks = std::min<int64_t>((a.nwt + 7) / 8, (int64_t)c->nsm * 8);
+            k_half_epilogue<ONE><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+            c->kernels += 1;
+        }
     } else {
         const int block = c->block ? std::min(c->block, kBlock64) : kBlock64;
         static std::atomic<int> grid_cache[kMaxWarps + 1] = {};  // per CTA size
@@ -1148,6 +1206,10 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
 template <bool MIXED>
 cudaError_t launch_force_m(md_ctx *c, const ForceArgs &a) {
     const bool one = c->hpair.nt == 1;
+    if (MIXED && c->params.half_list) {  // 4 lanes per atom (checked at create)
+        return one ? launch_force_t<true, 4, true, true>(c, a)
+                   : launch_force_t<true, 4, false, true>(c, a);
+    }
     switch (c->T) {
         case 1: return one ? launch_force_t<MIXED, 1, true>(c, a) : launch_force_t<MIXED, 1, false>(c, a);
         case 2: return one ? launch_force_t<MIXED, 2, true>(c, a) : launch_force_t<MIXED, 2, false>(c, a);
@@ -1186,6 +1248,7 @@ cudaError_t launch_force(md_ctx *c, int mode) {
     a.thermo_every = c->params.thermo_every;
     a.done = &c->dflags->done;
     a.tx_extra = c->debug_tx_extra;
+    a.facc = c->facc;
     cudaError_t e = c->params.precision == MD_MIXED ? launch_force_m<true>(c, a)
                                                     : launch_force_m<false>(c, a);
     if (e == cudaSuccess && mode == MODE_FUSED) c->pc ^= 1;

@@ -57,6 +57,8 @@ struct BuildArgs {
     double rs2;
     float rs2f, bandf;
     int pad, R;
+    int half;  // 1: keep pair (i, j) only if j's cell is forward of i's (code > 13) or
+               // it is i's cell and j comes after i
     int32_t *nn;
     uint32_t *nbr;
     Flags *fl;
@@ -225,6 +227,17 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
                     const unsigned bl1 = __ballot_sync(0xffffffffu, r21 < lo);
                     if (lane == 0) s_mask[w][hh] = make_uint4(bh0, bl0, bh1, bl1);
                 }
+                // half lists: candidates of a forward stencil cell, and of the
+                // home cell (staged in slot order)
+                unsigned fw0 = 0u, fw1 = 0u, hc0 = 0u, hc1 = 0u;
+                if (a.half) {
+                    const unsigned k0 = __float_as_uint(c0.w) >> MD_IDX_BITS;
+                    const unsigned k1 = __float_as_uint(c1.w) >> MD_IDX_BITS;
+                    fw0 = __ballot_sync(0xffffffffu, k0 > kCodeZero);
+                    fw1 = __ballot_sync(0xffffffffu, k1 > kCodeZero);
+                    hc0 = __ballot_sync(0xffffffffu, k0 == kCodeZero);
+                    hc1 = __ballot_sync(0xffffffffu, k1 == kCodeZero);
+                }
                 __syncwarp();
                 if (!active) continue;
                 const uint4 m = s_mask[w][lane];
@@ -233,6 +246,19 @@ __global__ void __launch_bounds__(kWarps * 32, MD_BUILD_MINB) k_build(BuildArgs 
                 const unsigned d0 = (unsigned)(self - g0), d1 = (unsigned)(self - g0 - 32);
                 if (d0 < 32u) { hi0 &= ~(1u << d0); lo0 &= ~(1u << d0); }
                 if (d1 < 32u) { hi1 &= ~(1u << d1); lo1 &= ~(1u << d1); }
+                if (a.half) {
+                    // home-cell candidates after the atom itself: window
+                    // positions above its own (the sentinel padding has code 13
+                    // but is never accepted)
+                    auto after = [&](int base) -> unsigned {
+                        const int k = self - base;  // the atom's bit in this half
+                        if (k < 0) return 0xffffffffu;
+                        if (k >= 31) return 0u;
+                        return ~((2u << k) - 1u);
+                    };
+                    const unsigned keep0 = fw0 | (hc0 & after(g0)), keep1 = fw1 | (hc1 & after(g0 + 32));
+                    hi0 &= keep0; lo0 &= keep0; hi1 &= keep1; lo1 &= keep1;
+                }
                 write_chunk(g0, hi0, lo0);
                 write_chunk(g0 + 32, hi1, lo1);
             }
@@ -317,6 +343,7 @@ cudaError_t launch_build(md_ctx *c) {
     a.bandf = c->hpair.bandf;
     a.pad = c->pad;
     a.R = c->R;
+    a.half = c->params.half_list ? 1 : 0;
     a.nn = c->nn;
     a.nbr = c->nbr;
     a.fl = c->dflags;

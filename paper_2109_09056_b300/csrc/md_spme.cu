@@ -1149,6 +1149,7 @@ md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md
     *out = nullptr;
     if (!c || !q || !p) return sfail(nullptr, MD_ERR_ARG, "NULL argument");
     if (c->nbox != 1) return sfail(nullptr, MD_ERR_ARG, "SPME needs a single-box context");
+    if (c->params.half_list) return sfail(nullptr, MD_ERR_ARG, "SPME needs full lists");
     if (!(p->alpha > 0.0) || !std::isfinite(p->alpha))
         return sfail(nullptr, MD_ERR_ARG, "alpha must be positive and finite");
     if (!(p->rc > 0.0) || !(p->rc <= c->params.rc))
