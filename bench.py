@@ -185,8 +185,10 @@ FP64_NOMINAL_TFLOPS = 1.25
 # read-modify-write (3 R).  Gather, per atom: r, cell, id, charge, real-space
 # force in (64 B), force out (24 B); per grid point one read (R).  Influence,
 # per half-spectrum element: Qhat read and written (4 R), theta read (R).
-# FFTs: the grid read and the half spectrum written, or back (R + 2 R per
-# element pair, counted on the grid and the half spectrum).  Real space:
+# FFTs (the forward x and y passes; the inverse y and x passes): the grid read
+# and the half spectrum written, or back, once (R per grid point + 2 R per
+# half-spectrum element; the passes move each element twice).  Influence (the
+# fused z pass: forward z, theta, inverse z): Qhat read and written, theta read.  Real space:
 # 4 B per list entry, and per atom its shadow or FP64 position, charge and
 # count in, its force out.
 SPME_SPREAD_ATOM, SPME_GATHER_ATOM = 52.0, 88.0

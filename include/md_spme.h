@@ -53,7 +53,8 @@ typedef struct {
     double rc;        /* real-space cutoff, 0 < rc <= the context's md_params.rc, so
                          that the context's list (rc + skin) holds every real-space pair
                          under the same displacement condition as the LJ forces */
-    int32_t K[3];     /* reciprocal grid points along x, y, z: order <= K_d <= 4096 */
+    int32_t K[3];     /* reciprocal grid points along x, y, z: order <= K_d <= 4096, each a
+                         product of 2s, 3s, 5s and 7s (the FFTs' radices), else MD_ERR_ARG */
     int32_t order;    /* B-spline order p: 4, 6 or 8 (even: the Euler-spline
                          moduli of an odd order vanish at m = K/2 for even K) */
 } md_spme_params;

@@ -5,8 +5,8 @@
 (run by path: importing the package first would load an older library).
 
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
-paper_2109_09056_b300/libmd_b300.so against the CUDA runtime and cuFFT (the
-3-D FFTs of the SPME long-range solver).
+paper_2109_09056_b300/libmd_b300.so against the CUDA runtime (no other
+library: the SPME solver's 3-D FFTs are the library's own kernels).
 """
 from __future__ import annotations
 
@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, extra=(), lib: str = LIB,
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         objs = list(ex.map(one, _sources()))
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, *extra, "-shared", "-o", tmp, *objs, "-lcufft", "-lcudart"]
+    cmd = [cc, *ARCH, *extra, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

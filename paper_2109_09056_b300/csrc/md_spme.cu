@@ -9,9 +9,8 @@
 //
 // Grid precision R follows the context: FP64 for MD_FP64 contexts; FP32 for
 // MD_MIXED (FP32 spline weights, grid, single-precision FFTs and gather, FP64
-// energy sums and force output).  B300's FP64 pipe runs at ~1/64 of FP32, and
-// a 384^3 double-precision FFT pair alone took 15 ms there, against the
-// memory-bound few tenths of a millisecond of the FP32 pair.
+// energy sums and force output).  B300's FP64 pipe runs at ~1/64 of FP32, so
+// the FP64 FFTs are bound there, the FP32 ones by memory.
 //
 // One md_spme_compute is these launches on the context's stream:
 //   k_spme_charges  charge of each slot's atom, gathered by its original id
@@ -23,11 +22,13 @@
 //   k_spme_real     the real-space erfc pairs over the context's Verlet list
 //                   (same warp-transposed rows and lanes per atom as the LJ
 //                   kernels), FP64 or FP32 + Kahan by the context's precision;
-//   cuFFT R2C / D2Z Q -> Qhat (half spectrum, K_z x K_y x (K_x/2+1));
-//   k_spme_influence  per half-spectrum element: energy term theta |Qhat|^2
-//                   (weighted 2 for the elements that stand for a conjugate
-//                   pair), then Qhat *= theta;
-//   cuFFT C2R / Z2D -> dE/dQ on the grid (unnormalised inverse);
+//   k_fft_x_r2c, k_fft_lines  the forward FFT's x and y passes: Q -> Qhat
+//                   (half spectrum, K_z x K_y x (K_x/2+1));
+//   k_fft_z_influence  the z pass: each z line forward, its energy terms
+//                   theta |Qhat|^2 (weighted 2 for the elements that stand for
+//                   a conjugate pair), Qhat *= theta, back along z;
+//   k_fft_lines, k_fft_x_c2r  the inverse's y and x passes -> dE/dQ on the
+//                   grid (unnormalised inverse) (md_fft.cu, hand-written);
 //   k_spme_gather   one thread per slot: spline gradients against dE/dQ, plus the
 //                   slot's real-space force, written in original atom order;
 // then one single-CTA sum of the energy partials (fixed order, deterministic).
@@ -42,7 +43,7 @@
 // evaluation whose real-space pass is fused with the LJ pair terms (one walk
 // of the list writes F_LJ + F_real; the gather adds F_recip), then
 // k_spme_half_kick closes the step.
-#include <cufft.h>
+#include "md_fft.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -152,8 +153,7 @@ struct md_spme {
     int64_t f_step = -1, f_kernels = -1;
     int f_pc = -1, f_oc = -1;
     Pair f_pair{};
-    cufftHandle fwd = 0, bwd = 0;
-    bool have_fwd = false, have_bwd = false;
+    Fft3 fft;                   // the hand-written 3-D FFT passes (md_fft.cu)
     bool prof = false;
     cudaEvent_t ev[kEvents] = {};
     cudaStream_t side = nullptr;        // real-space pass beside the reciprocal chain
@@ -175,20 +175,10 @@ md_status scuda(md_spme *s, cudaError_t e, const char *where) {
                  std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-md_status sfft(md_spme *s, cufftResult r, const char *where) {
-    return sfail(s, r == CUFFT_ALLOC_FAILED ? MD_ERR_NOMEM : MD_ERR_CUDA,
-                 std::string(where) + ": cuFFT error " + std::to_string((int)r));
-}
-
 #define SCK(call)                                               \
     do {                                                        \
         cudaError_t e_ = (call);                                \
         if (e_ != cudaSuccess) return scuda(s, e_, #call);      \
-    } while (0)
-#define FCK(call)                                               \
-    do {                                                        \
-        cufftResult r_ = (call);                                \
-        if (r_ != CUFFT_SUCCESS) return sfft(s, r_, #call);     \
     } while (0)
 
 // ---- B-splines --------------------------------------------------------------
@@ -458,27 +448,6 @@ __global__ void __launch_bounds__(kThreads) k_spme_half_kick(const Box *__restri
 template <typename R> struct Cplx;
 template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
-
-// Half-spectrum element h = (m_z K_y + m_y) Kh + m_x: energy term and Qhat *= theta.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_spme_influence(typename Cplx<R>::T *__restrict__ ghat,
-                                                             const R *__restrict__ theta,
-                                                             int64_t nhalf, int Kh, int Kx,
-                                                             double *__restrict__ part) {
-    double e = 0.0;
-    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < nhalf;
-         h += (int64_t)gridDim.x * blockDim.x) {
-        const int mx = (int)(h % Kh);
-        const R wgt = (mx == 0 || 2 * mx == Kx) ? R(1) : R(2);
-        const R th = theta[h];
-        auto v = ghat[h];
-        e += (double)(wgt * th * (v.x * v.x + v.y * v.y));
-        v.x *= th;
-        v.y *= th;
-        ghat[h] = v;
-    }
-    cta_sum_to<kThreads>(e, part + blockIdx.x);
-}
 
 // theta(m) = B(m) exp(-pi^2 |m|^2 / alpha^2) / (pi V |m|^2), theta(0) = 0, on
 // the half spectrum; bmod holds |b_x|^2 (K_x), |b_y|^2 (K_y), |b_z|^2 (K_z).
@@ -1011,8 +980,7 @@ void destroy(md_spme *s) {
     F(s->q); F(s->qs); F(s->shq); F(s->grid); F(s->ghat); F(s->theta); F(s->fs); F(s->part); F(s->lpart);
     F(s->dsum); F(s->fstage); F(s->kpart); F(s->tab64);
     if (s->hsum) cudaFreeHost(s->hsum);
-    if (s->have_fwd) cufftDestroy(s->fwd);
-    if (s->have_bwd) cufftDestroy(s->bwd);
+    fft3_free(&s->fft);
     for (auto e : s->ev)
         if (e) cudaEventDestroy(e);
     if (s->fork) cudaEventDestroy(s->fork);
@@ -1130,12 +1098,7 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
         SCK(cudaMemcpy(s->tab64, h64.data(), kTab64 * sizeof(double), cudaMemcpyHostToDevice));
     }
     if (s->f32) fit_erfc_mixed(s, p->alpha, p->rc);
-    FCK(cufftPlan3d(&s->fwd, g.K[2], g.K[1], g.K[0], s->f32 ? CUFFT_R2C : CUFFT_D2Z));
-    s->have_fwd = true;
-    FCK(cufftPlan3d(&s->bwd, g.K[2], g.K[1], g.K[0], s->f32 ? CUFFT_C2R : CUFFT_Z2D));
-    s->have_bwd = true;
-    FCK(cufftSetStream(s->fwd, c->stream));
-    FCK(cufftSetStream(s->bwd, c->stream));
+    SCK(fft3_plan(&s->fft, g.K, s->f32));
     return load_charges(s, q);
 }
 
@@ -1156,9 +1119,13 @@ md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md
         return sfail(nullptr, MD_ERR_ARG, "rc must satisfy 0 < rc <= the context's pair cutoff");
     if (p->order != 4 && p->order != 6 && p->order != 8)
         return sfail(nullptr, MD_ERR_ARG, "order must be 4, 6 or 8");
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d) {
         if (p->K[d] < p->order || p->K[d] > kMaxGrid)
             return sfail(nullptr, MD_ERR_ARG, "grid size K out of [order, 4096]");
+        int rad[kFftMaxStages], nst = 0;
+        if (!fft_factor(p->K[d], true, rad, &nst))
+            return sfail(nullptr, MD_ERR_ARG, "grid size K must factor into 2, 3, 5 and 7");
+    }
     md_spme *s = new (std::nothrow) md_spme();
     if (!s) return sfail(nullptr, MD_ERR_NOMEM, "host allocation failed");
     md_status st = init(s, c, q, p);
@@ -1268,25 +1235,12 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     SCK(mark(1));
     if (!overlap) SCK(launch_real(mixed, lj, c->T, ra, real_blocks, stream));
     SCK(mark(2));
-    if (s->f32)
-        FCK(cufftExecR2C(s->fwd, (cufftReal *)s->grid, (cufftComplex *)s->ghat));
-    else
-        FCK(cufftExecD2Z(s->fwd, (cufftDoubleReal *)s->grid, (cufftDoubleComplex *)s->ghat));
+    SCK(fft3_forward_xy(s->fft, s->grid, s->ghat, stream));
     SCK(mark(3));
-    if (s->f32)
-        k_spme_influence<float><<<(int)s->nrecip, kThreads, 0, stream>>>(
-            (float2 *)s->ghat, (const float *)s->theta, s->nhalf, s->g.Kh, s->g.K[0],
-            s->part + real_blocks);
-    else
-        k_spme_influence<double><<<(int)s->nrecip, kThreads, 0, stream>>>(
-            (double2 *)s->ghat, (const double *)s->theta, s->nhalf, s->g.Kh, s->g.K[0],
-            s->part + real_blocks);
-    SCK(cudaGetLastError());
+    SCK(fft3_z_influence(s->fft, s->ghat, s->theta, s->part + real_blocks, (int)s->nrecip,
+                         stream));
     SCK(mark(4));
-    if (s->f32)
-        FCK(cufftExecC2R(s->bwd, (cufftComplex *)s->ghat, (cufftReal *)s->grid));
-    else
-        FCK(cufftExecZ2D(s->bwd, (cufftDoubleComplex *)s->ghat, (cufftDoubleReal *)s->grid));
+    SCK(fft3_inverse_yx(s->fft, s->ghat, s->grid, stream));
     SCK(mark(5));
     if (overlap) SCK(cudaStreamWaitEvent(stream, s->join, 0));
     SCK(launch_atoms_any(s->f32, s->p.order, acc ? kGatherAcc : kGatherOut, aa, s->qs, s->grid,
@@ -1294,7 +1248,9 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     SCK(mark(6));
     k_spme_sum<<<1, 1024, 0, stream>>>(s->part, real_blocks, s->nrecip, s->dsum);
     SCK(cudaGetLastError());
-    c->kernels += 6;  // charges, real space, spread, influence, gather, sum (cuFFT's own aside)
+    // charges, real space, spread, 2 forward FFT passes, the z pass with the
+    // influence function, 2 inverse passes, gather, sum
+    c->kernels += 10;
     return MD_OK;
 }
 

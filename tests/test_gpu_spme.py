@@ -65,6 +65,22 @@ def test_spme_parity_orders(precision, order):
     sysm.close()
 
 
+@pytest.mark.parametrize("K", [(45, 42, 35), (49, 28, 30), (16, 64, 27)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_fft_radices(precision, K):
+    """Every FFT radix on every axis: an odd K_x (the half spectrum's last
+    element then stands for a conjugate pair), radix 7 (45 = 3 3 5, 42 = 2 3 7,
+    35 = 5 7, 49 = 7 7, 28 = 4 7, 30 = 2 3 5) and pure radix 8 / 4 / 3 axes."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    order = 4
+    sysm = make(s, precision)
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=K, order=order)
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, K, order, precision)
+    sp.close()
+    sysm.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_spme_after_steps_and_device_output(precision):
     cs = mi.charged_workload("coulomb_fcc10_4000")
@@ -126,7 +142,9 @@ def test_spme_argument_checks():
            dict(alpha=cs.alpha, rc=3.0, K=40, order=4),          # rc above the pair cutoff
            dict(alpha=0.0, rc=cs.rc, K=40, order=4),
            dict(alpha=cs.alpha, rc=cs.rc, K=(40, 3, 40), order=4),
-           dict(alpha=cs.alpha, rc=cs.rc, K=(40, 40, 5000), order=4)]
+           dict(alpha=cs.alpha, rc=cs.rc, K=(40, 40, 5000), order=4),
+           dict(alpha=cs.alpha, rc=cs.rc, K=(40, 41, 40), order=4),  # 41: no radix
+           dict(alpha=cs.alpha, rc=cs.rc, K=(40, 40, 44), order=4)]  # 44 = 4 11
     for kw in bad:
         with pytest.raises(MDError) as ei:
             SPME(sysm, cs.q, **kw)
