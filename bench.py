@@ -299,8 +299,10 @@ def spme_leg(args, stream, hbm_peak):
 def variants_leg(sysd, stream, hbm_peak):
     """Traversal / list-layout variants of the LJ step on the benchmark
     workload: the team size of the hierarchical traversal (lanes per atom,
-    which also fixes the list's warp-transposed layout) at 1, 2, 4 and 8, and
-    half lists (each pair once, reactions by atomics; 4 lanes).  Per variant:
+    which also fixes the list's warp-transposed layout) at 1, 2, 4 and 8, half
+    lists (each pair once, reactions by atomics; 4 lanes), and the particle
+    layout of the neighbor gathers (AoSoA of vector length 8 and 32 against
+    the float4 shadow; 4 lanes; the AoSoA copy's refresh counted).  Per variant:
     the force evaluation's device ms per launch (profiled launches, CUDA
     events; with half lists the force kernel and its epilogue kernel), its HBM
     fraction over its own algorithmic bytes, and the whole step's throughput
@@ -308,12 +310,16 @@ def variants_leg(sysd, stream, hbm_peak):
     import torch
 
     from paper_2109_09056_b300 import MDSystem
-    res = {"workload": "see config", "axis": "lanes_per_atom (half: 4 lanes, half lists)",
+    res = {"workload": "see config",
+           "axis": "lanes_per_atom; half: 4 lanes, half lists; aosoaV: 4 lanes, neighbor "
+                   "gathers from an AoSoA shadow copy of vector length V",
            "md_steps": 2 * MD_PER_STEP}
-    for lanes in (1, 2, 4, 8, "half"):
+    for lanes in (1, 2, 4, 8, "half", "aosoa8", "aosoa32"):
+        named = isinstance(lanes, str)
         m = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", rc=sysd.rc,
                      skin=sysd.skin, dt=sysd.dt, rebuild_every=sysd.rebuild_every,
-                     lanes_per_atom=4 if lanes == "half" else lanes, half_list=lanes == "half",
+                     lanes_per_atom=4 if named else lanes, half_list=lanes == "half",
+                     shadow_vl=int(lanes[5:]) if named and lanes.startswith("aosoa") else 0,
                      stream=stream)
         m.step(MD_PER_STEP)
         m.profile(True)

@@ -89,6 +89,13 @@ typedef struct {
                                     forces are then reproducible to rounding, not bitwise;
                                     md_force_backward and md_spme_create refuse such a
                                     context.  0: full lists (default). */
+    int32_t shadow_vl;           /* layout the mixed force kernel gathers neighbor positions
+                                    from: 0 = one float4 (x, y, z, type) per atom (default);
+                                    8 or 32 = blocks of that many atoms holding x[], y[],
+                                    z[], type[] in turn (AoSoA), refreshed from the float4
+                                    shadows before each force evaluation; mixed precision
+                                    with 4 lanes per atom and full lists only (else
+                                    MD_ERR_ARG).  Same forces bit for bit. */
 } md_params;
 
 /* Fills p with the classic LJ-melt settings: 1 type, eps = sigma = m = 1,

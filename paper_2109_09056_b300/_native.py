@@ -43,7 +43,8 @@ class md_params(C.Structure):
                 ("shift_energy", C.c_int32), ("check_displacement", C.c_int32),
                 ("thermo_every", C.c_int32), ("neigh_pad", C.c_int32),
                 ("lanes_per_atom", C.c_int32), ("block_threads", C.c_int32),
-                ("use_graphs", C.c_int32), ("half_list", C.c_int32)]
+                ("use_graphs", C.c_int32), ("half_list", C.c_int32),
+                ("shadow_vl", C.c_int32)]
 
 
 class md_thermo(C.Structure):

@@ -91,7 +91,7 @@ def md_params_default() -> N.md_params:
 def make_params(ntypes=1, eps=None, sigma=None, mass=None, rc=2.5, skin=0.3, dt=0.005,
                 rebuild_every=20, precision="mixed", shift_energy=False,
                 check_displacement=False, thermo_every=0, neigh_pad=0, lanes_per_atom=0,
-                block_threads=0, use_graphs=True, half_list=False):
+                block_threads=0, use_graphs=True, half_list=False, shadow_vl=0):
     """md_params plus the arrays it points to (keep both alive together)."""
     eps = np.ascontiguousarray(np.ones((ntypes, ntypes)) if eps is None else eps, dtype=np.float64)
     sigma = np.ascontiguousarray(np.ones((ntypes, ntypes)) if sigma is None else sigma,
@@ -114,6 +114,7 @@ def make_params(ntypes=1, eps=None, sigma=None, mass=None, rc=2.5, skin=0.3, dt=
     p.block_threads = int(block_threads)
     p.use_graphs = int(bool(use_graphs))
     p.half_list = int(bool(half_list))
+    p.shadow_vl = int(shadow_vl)
     return p, (eps, sigma, mass)
 
 
@@ -379,12 +380,12 @@ class MDSystem:
     def __init__(self, x, v, types, box, *, ntypes=1, eps=None, sigma=None, mass=None, rc=2.5,
                  skin=0.3, dt=0.005, rebuild_every=20, precision="mixed", shift_energy=False,
                  check_displacement=False, thermo_every=0, neigh_pad=0, lanes_per_atom=0,
-                 block_threads=0, use_graphs=True, half_list=False, stream=None, n_per_box=None,
-                 boxes=None):
+                 block_threads=0, use_graphs=True, half_list=False, shadow_vl=0, stream=None,
+                 n_per_box=None, boxes=None):
         self.params, self._arrays = make_params(
             ntypes, eps, sigma, mass, rc, skin, dt, rebuild_every, precision, shift_energy,
             check_displacement, thermo_every, neigh_pad, lanes_per_atom, block_threads, use_graphs,
-            half_list)
+            half_list, shadow_vl)
         if stream is None and torch is not None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()
         self.stream = stream

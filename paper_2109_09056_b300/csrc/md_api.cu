@@ -67,7 +67,7 @@ void free_all(md_ctx *c) {
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
     F(c->tpart); F(c->tbox); F(c->fpart); F(c->tlog); F(c->dscratch); F(c->stage);
-    F(c->restage); F(c->scan_part); F(c->ctab); F(c->facc);
+    F(c->restage); F(c->scan_part); F(c->ctab); F(c->facc); F(c->shv);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -298,6 +298,9 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
         return fail(c, MD_ERR_ARG, "lanes_per_atom must be 1, 2, 4 or 8");
     if (p.half_list && (p.precision != MD_MIXED || c->T != 4))
         return fail(c, MD_ERR_ARG, "half_list needs MD_MIXED and 4 lanes per atom");
+    if (p.shadow_vl != 0 && ((p.shadow_vl != 8 && p.shadow_vl != 32) || p.precision != MD_MIXED ||
+                             c->T != 4 || p.half_list))
+        return fail(c, MD_ERR_ARG, "shadow_vl must be 0, or 8 or 32 with MD_MIXED, 4 lanes, full lists");
     c->block = p.block_threads;  // 0: chosen per launch (md_force.cu)
     if (c->block != 0 && (c->block < 64 || c->block > 768 || c->block % 32))
         return fail(c, MD_ERR_ARG, "block_threads must be 0 or 64..768, a multiple of 32");
@@ -370,6 +373,10 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     }
     CK(dalloc(&c->f, 3 * ns));
     CK(cudaMemset(c->f, 0, 3 * ns * sizeof(double)));
+    if (p.shadow_vl) {
+        const size_t blocks = (ns + 1 + p.shadow_vl - 1) / p.shadow_vl;
+        CK(dalloc(&c->shv, blocks * 4 * (size_t)p.shadow_vl));
+    }
     if (p.half_list) {  // kept at zero between force evaluations
         CK(dalloc(&c->facc, ns + 1));
         CK(cudaMemset(c->facc, 0, (ns + 1) * sizeof(float4)));

@@ -61,7 +61,22 @@ struct ForceArgs {
     unsigned int *done;
     uint32_t tx_extra;  // test hook: list-copy bytes that never arrive (0 normally)
     float4 *facc;       // half lists: force (x, y, z) and energy accumulators per slot
+    const float *shv;   // shadow_vl > 0: the shadows in blocks of x[VL], y[VL], z[VL], type[VL]
 };
+
+// Neighbor j's shadow for the mixed kernels: one 16-byte load from the float4
+// array (VL = 0), or from the AoSoA copy, one 4-byte load per component (the
+// type only when there are several).
+template <int VL, bool ONE>
+__device__ __forceinline__ float4 gather_shadow(const ForceArgs &a, uint32_t en) {
+    const int64_t j = chk_index(en & MD_IDX_MASK, a.ns + 1, CHK_FORCE_GATHER, a.fl, a.ns);
+    if constexpr (VL == 0) {
+        return __ldg(a.sh_in + j);
+    } else {
+        const float *p = a.shv + (j / VL) * (4 * VL) + (j % VL);
+        return make_float4(__ldg(p), __ldg(p + VL), __ldg(p + 2 * VL), ONE ? 0.f : __ldg(p + 3 * VL));
+    }
+}
 
 // Half lists: add (x, y, z, e) to slot j's accumulator (one vector reduction).
 __device__ __forceinline__ void red_add4(float4 *p, float x, float y, float z, float e) {
@@ -495,7 +510,7 @@ struct Acc {
 // the warp's stencil offsets (off[d][code]).  HALF: each entry is a pair
 // listed once; its reaction (and half its energy) goes to the partner's
 // accumulator.
-template <bool ONE, bool THERMO, bool HALF>
+template <bool ONE, bool THERMO, bool HALF, int VL = 0>
 __device__ __forceinline__ void lane_rows(const ForceArgs &a, const SmemTabs &tb,
                                           const MixedConst &k, const float (*off)[32],
                                           const uint32_t *Lr, int rows, const float4 &si, int ti,
@@ -563,15 +578,12 @@ __device__ __forceinline__ void lane_rows(const ForceArgs &a, const SmemTabs &tb
         for (int u = 0; u < kBatch; ++u) eb[u] = Lr[(q + u) * 32];
         float4 sj[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            sj[u] = __ldg(a.sh_in + chk_index(eb[u] & MD_IDX_MASK, a.ns + 1, CHK_FORCE_GATHER,
-                                              a.fl, a.ns));
+        for (int u = 0; u < kBatch; ++u) sj[u] = gather_shadow<VL, ONE>(a, eb[u]);
         batch(eb, sj);
     }
     for (int q = rows_full; q < rows; ++q) {
         const uint32_t en = Lr[q * 32];
-        const float4 sj = __ldg(a.sh_in + chk_index(en & MD_IDX_MASK, a.ns + 1,
-                                                    CHK_FORCE_GATHER, a.fl, a.ns));
+        const float4 sj = gather_shadow<VL, ONE>(a, en);
         float tx, ty, tz, tp;
         terms(en, sj, tx, ty, tz, tp);
         kahan_add(acc.fx, acc.cx, tx);
@@ -589,7 +601,7 @@ __device__ __forceinline__ void set_offsets(float (*off)[32], const Box &B, int 
     off[2][lane] = code ? (float)(lane / 9 - 1) * B.hf[2] : 0.f;
 }
 
-template <int T, bool ONE, bool THERMO, bool HALF>
+template <int T, bool ONE, bool THERMO, bool HALF, int VL>
 __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &tb,
                                            float (*s_off)[3][32], uint64_t (*s_bar)[2],
                                            uint32_t *lbuf) {
@@ -671,7 +683,7 @@ __device__ __forceinline__ void mixed_body(const ForceArgs &a, const SmemTabs &t
         phase ^= 1u << cb;
         __syncwarp();  // s_off is visible to the whole warp
         Acc acc;
-        lane_rows<ONE, THERMO, HALF>(a, tb, kc, s_off[wib],
+        lane_rows<ONE, THERMO, HALF, VL>(a, tb, kc, s_off[wib],
                                lbuf + (size_t)wib * 2 * rowblk + cb * rowblk + lane, rows_cur, si,
                                ti, acc);
         __syncwarp();  // done reading this half; the next copy may refill it
@@ -899,7 +911,7 @@ __device__ __forceinline__ void kernel_done(const ForceArgs &a, int64_t clock, b
 #define MD_FORCE_MAXREG (65536 / (MD_FORCE_MINB * 128) / 8 * 8)
 static_assert(MD_FORCE_MAXREG * kMaxWarpsMixed * 32 <= 65536, "a full-size CTA must fit the SM");
 
-template <int T, bool ONE, bool HALF>
+template <int T, bool ONE, bool HALF, int VL>
 __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
         if (!HALF) mirror_state(a);  // half lists: the epilogue kernel mirrors
@@ -917,10 +929,26 @@ __global__ void __maxnreg__(MD_FORCE_MAXREG) k_force_mixed(ForceArgs a) {
         if (thermo) mixed_body_pairs<ONE, true>(a, tb, s_off, s_bar, lbuf);
         else mixed_body_pairs<ONE, false>(a, tb, s_off, s_bar, lbuf);
     } else {
-        if (thermo) mixed_body<T, ONE, true, HALF>(a, tb, s_off, s_bar, lbuf);
-        else mixed_body<T, ONE, false, HALF>(a, tb, s_off, s_bar, lbuf);
+        if (thermo) mixed_body<T, ONE, true, HALF, VL>(a, tb, s_off, s_bar, lbuf);
+        else mixed_body<T, ONE, false, HALF, VL>(a, tb, s_off, s_bar, lbuf);
     }
     if (!HALF) kernel_done(a, clock, thermo);
+}
+
+// The AoSoA copy of the shadows (slots 0..ns, the sentinel's included): slot i
+// in block i / VL at lane i % VL of each component array.
+template <int VL>
+__global__ void k_shadow_aosoa(const float4 *__restrict__ sh, float *__restrict__ shv, int64_t m,
+                               const Flags *fl) {
+    if (fl->status & ST_FREEZE) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float4 s = sh[i];
+    float *p = shv + (i / VL) * (4 * VL) + (i % VL);
+    p[0] = s.x;
+    p[VL] = s.y;
+    p[2 * VL] = s.z;
+    p[3 * VL] = s.w;
 }
 
 // Half lists, after k_force_mixed<4, ONE, true>: each slot's accumulator holds
@@ -1133,7 +1161,7 @@ int auto_block_mixed(const md_ctx *c, int64_t nwt, size_t per_warp_smem) {
     return 64;
 }
 
-template <bool MIXED, int T, bool ONE, bool HALF = false>
+template <bool MIXED, int T, bool ONE, bool HALF = false, int VL = 0>
 cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
     if constexpr (MIXED) {
         // Each warp has a double buffer of R list rows in shared memory (of two
@@ -1155,14 +1183,14 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
             std::lock_guard<std::mutex> lock(mu);
             if (smem > smem_set) {
                 cudaError_t e = cudaFuncSetAttribute(
-                    k_force_mixed<T, ONE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    k_force_mixed<T, ONE, HALF, VL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 smem_set = smem;
             }
             if (occ_smem != smem || occ_block != block) {
                 int per = 0;
                 cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per, k_force_mixed<T, ONE, HALF>, block, smem);
+                    &per, k_force_mixed<T, ONE, HALF, VL>, block, smem);
                 if (e != cudaSuccess) return e;
                 occ = per > 0 ? per : 1;
                 occ_smem = smem;
@@ -1174,7 +1202,13 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         const int64_t need = (units + warps - 1) / warps;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
-        k_force_mixed<T, ONE, HALF><<<(unsigned)grid, block, smem, c->stream>>>(a);
+        if constexpr (VL > 0) {
+            const int64_t m = c->ns + 1;
+            k_shadow_aosoa<VL><<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(a.sh_in, c->shv,
+                                                                                   m, a.fl);
+            c->kernels += 1;
+        }
+        k_force_mixed<T, ONE, HALF, VL><<<(unsigned)grid, block, smem, c->stream>>>(a);
         if constexpr (HALF) {
             const int64_t blocks = std::min<int64_t>((a.nwt + 7) / 8, (int64_t)c->nsm * 8);
             k_half_epilogue<ONE><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
@@ -1209,6 +1243,14 @@ cudaError_t launch_force_m(md_ctx *c, const ForceArgs &a) {
     if (MIXED && c->params.half_list) {  // 4 lanes per atom (checked at create)
         return one ? launch_force_t<true, 4, true, true>(c, a)
                    : launch_force_t<true, 4, false, true>(c, a);
+    }
+    if (MIXED && c->params.shadow_vl == 8) {  // 4 lanes per atom (checked at create)
+        return one ? launch_force_t<true, 4, true, false, 8>(c, a)
+                   : launch_force_t<true, 4, false, false, 8>(c, a);
+    }
+    if (MIXED && c->params.shadow_vl == 32) {
+        return one ? launch_force_t<true, 4, true, false, 32>(c, a)
+                   : launch_force_t<true, 4, false, false, 32>(c, a);
     }
     switch (c->T) {
         case 1: return one ? launch_force_t<MIXED, 1, true>(c, a) : launch_force_t<MIXED, 1, false>(c, a);
@@ -1249,6 +1291,7 @@ cudaError_t launch_force(md_ctx *c, int mode) {
     a.done = &c->dflags->done;
     a.tx_extra = c->debug_tx_extra;
     a.facc = c->facc;
+    a.shv = c->shv;
     cudaError_t e = c->params.precision == MD_MIXED ? launch_force_m<true>(c, a)
                                                     : launch_force_m<false>(c, a);
     if (e == cudaSuccess && mode == MODE_FUSED) c->pc ^= 1;

@@ -137,7 +137,8 @@ struct md_spme {
     double *tab64 = nullptr;    // FP64 pair-function polynomials (kTab64)
     float erfc_c[kErfcDeg + 1] = {};  // mixed: H's coefficients in s (see kErfcDeg)
     float erfc_sa = 0.f, erfc_sb = 0.f;  // s = sa t + sb
-    bool erfc_fit = false;      // H met kErfcTol (else erfcf)
+    bool erfc_fit = false;      // use H (else erfcf): see fit_erfc_mixed
+    double erfc_err[2] = {0, 0};  // device check: max relative error of H's form, of erfcf
     double *part = nullptr;     // energy partials: real [nreal], then recip [nrecip]
     double *lpart = nullptr;    // LJ energy partials of the fused pass [nreal]
     int64_t nreal = 0, nrecip = 0;
@@ -520,6 +521,31 @@ __device__ __forceinline__ float erfc_mixed(const RealArgs &a, float x, float ex
     return ex * (t * h);
 }
 
+// The mixed pass's erfc(alpha r) as the real-space kernel evaluates it (the
+// same FP32 operations and intrinsics, from r^2 in FP32), by the fitted form
+// and by erfcf, against FP64 erfc of the same r: the largest relative errors
+// over npts separations in (0, rc], into out[0] (fitted) and out[1] (erfcf)
+// as the bit patterns of non-negative doubles (which order as integers).
+__global__ void k_erfc_check(RealArgs a, double alpha, float rc, int npts,
+                             unsigned long long *out) {
+    double w_fit = 0.0, w_lib = 0.0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x + 1; q <= npts;
+         q += gridDim.x * blockDim.x) {
+        const float r = rc * (float)q / (float)npts;
+        const float r2 = r * r;
+        const float rinv = rsqrtf(r2);
+        const float ex = __expf(-(a.alphaf * a.alphaf) * r2);
+        const float x = a.alphaf * (r2 * rinv);
+        const double ref = erfc(alpha * sqrt((double)r2));
+        RealArgs f = a;
+        f.efit = 1;
+        w_fit = fmax(w_fit, fabs((double)erfc_mixed(f, x, ex) - ref) / ref);
+        w_lib = fmax(w_lib, fabs((double)erfcf(x) - ref) / ref);
+    }
+    atomicMax(out, (unsigned long long)__double_as_longlong(w_fit));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(w_lib));
+}
+
 // erfc(alpha r) and exp(-alpha^2 r^2) from the piecewise tables (Horner in
 // the interval's local coordinate t = r kPieces / rc - k), D the degree.
 template <typename V, int D>
@@ -889,6 +915,35 @@ void fit_erfc_mixed(md_spme *s, double alpha, double rc) {
     s->erfc_fit = worst <= kErfcTol;
 }
 
+// The device check of the fit (k_erfc_check): H's form is used when, as the
+// kernel evaluates it (__fdividef, __expf, FP32 arguments), it is within
+// kErfcTol of erfc or no worse than erfcf on the same inputs.
+md_status check_erfc_on_device(md_spme *s) {
+    if (!s->erfc_fit) return MD_OK;  // the host check already chose erfcf
+    RealArgs ra{};
+    ra.alphaf = (float)s->p.alpha;
+    for (int k = 0; k <= kErfcDeg; ++k) ra.ec[k] = s->erfc_c[k];
+    ra.esa = s->erfc_sa;
+    ra.esb = s->erfc_sb;
+    ra.efit = 1;
+    unsigned long long *d = nullptr;
+    SCK(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemset(d, 0, sizeof(h));
+    if (e == cudaSuccess) {
+        k_erfc_check<<<16, 256, 0, s->stream>>>(ra, s->p.alpha, (float)s->p.rc, 4000, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(d);
+    SCK(e);
+    std::memcpy(&s->erfc_err[0], &h[0], sizeof(double));
+    std::memcpy(&s->erfc_err[1], &h[1], sizeof(double));
+    s->erfc_fit = s->erfc_err[0] <= std::max(kErfcTol, s->erfc_err[1]);
+    return MD_OK;
+}
+
 template <int T, bool MIXED, bool LJ>
 cudaError_t launch_real_t(const RealArgs &ra, int blocks, cudaStream_t st) {
     k_spme_real<T, MIXED, LJ><<<blocks, kRealBlock, 0, st>>>(ra);
@@ -1097,7 +1152,11 @@ md_status init(md_spme *s, md_ctx *c, const double *q, const md_spme_params *p) 
         SCK(salloc(&s->tab64, kTab64));
         SCK(cudaMemcpy(s->tab64, h64.data(), kTab64 * sizeof(double), cudaMemcpyHostToDevice));
     }
-    if (s->f32) fit_erfc_mixed(s, p->alpha, p->rc);
+    if (s->f32) {
+        fit_erfc_mixed(s, p->alpha, p->rc);
+        const md_status se = check_erfc_on_device(s);
+        if (se != MD_OK) return se;
+    }
     SCK(fft3_plan(&s->fft, g.K, s->f32));
     return load_charges(s, q);
 }
