@@ -6,7 +6,8 @@ to the partner's accumulator.  Mixed precision, 4 lanes per atom.
 Bars: the half rows hold every pair once, and together with their reversals
 they are exactly the FP64 oracle's full list (integer sets, bit-exact); forces
 within relative L2 1e-5 of the oracle (the mixed bar) and potential energy to
-1e-5 for single boxes (2, 3 and 5 cells per axis); in a batch, forces to 1e-5
+1e-5 for single boxes (2, 3 and 5 cells per axis, and a compressed box whose
+home cells straddle the build's staging windows); in a batch, forces to 1e-5
 and energies against the full-list run; a 45-step run
 stays within 1e-6 of the full-list run; the calls that need full lists refuse
 a half-list context.
@@ -31,7 +32,15 @@ def boxes():
     rng = np.random.default_rng(4)
     return {"fcc10_nc5": mi.lj_melt(10, seed=21, jitter=0.2),
             "fcc6_nc3": mi.lj_melt(6, seed=3, jitter=0.1),
-            "vac250_nc2": mi.vacancy_box(250, 0.9, 1.2, rng)}
+            "vac250_nc2": mi.vacancy_box(250, 0.9, 1.2, rng),
+            # compressed lattice, 3 cells per axis, up to 62 atoms per cell: a
+            # home cell's atoms come in two 32-candidate chunks, and for several
+            # home batches the staging window fills between them, so the chunk
+            # before the batch's own atoms lies in an earlier window
+            "dense_fcc7_nc3": mi.lj_melt(7, rho=1.2, seed=1, jitter=0.1)}
+
+
+NAMES = ["fcc10_nc5", "fcc6_nc3", "vac250_nc2", "dense_fcc7_nc3"]
 
 
 def half_pairs_by_id(sysm):
@@ -47,7 +56,7 @@ def half_pairs_by_id(sysm):
     return pairs, int(nn.sum())
 
 
-@pytest.mark.parametrize("name", ["fcc10_nc5", "fcc6_nc3", "vac250_nc2"])
+@pytest.mark.parametrize("name", NAMES)
 def test_half_rows_hold_each_pair_once_and_symmetrize_to_the_oracle(name):
     s = boxes()[name]
     sysm = make(s, "mixed", half_list=True)
@@ -63,7 +72,7 @@ def test_half_rows_hold_each_pair_once_and_symmetrize_to_the_oracle(name):
     sysm.close()
 
 
-@pytest.mark.parametrize("name", ["fcc10_nc5", "fcc6_nc3", "vac250_nc2"])
+@pytest.mark.parametrize("name", NAMES)
 def test_half_list_forces_and_energy_match_the_oracle(name):
     s = boxes()[name]
     sysm = make(s, "mixed", half_list=True)
