@@ -122,7 +122,7 @@ md_status setup_pair(md_ctx *c, const double *eps, const double *sigma) {
     P.half_skin = 0.5 * p.skin;
     P.rc2f = (float)P.rc2;
     P.rs2f = (float)P.rs2;
-    P.bandf = (float)(3e-5 * P.rs2);  // > 20x the FP32 r^2 error bound (md_neigh.cu)
+    P.bandf = (float)(3e-5 * P.rs2);  // > 3.9x the FP32 r^2 error bound (md_neigh.cu)
     c->eps.assign(eps, eps + nt * nt);
     c->sigma.assign(sigma, sigma + nt * nt);
     for (int a = 0; a < nt; ++a)
