@@ -302,7 +302,9 @@ def variants_leg(sysd, stream, hbm_peak):
     which also fixes the list's warp-transposed layout) at 1, 2, 4 and 8, half
     lists (each pair once, reactions by atomics; 4 lanes), and the particle
     layout of the neighbor gathers (AoSoA of vector length 8 and 32 against
-    the float4 shadow; 4 lanes; the AoSoA copy's refresh counted).  Per variant:
+    the float4 shadow; 4 lanes; the AoSoA copy's refresh counted); and the FP64
+    path with full lists (its automatic lanes) and with half lists (FP64
+    atomics, 4 lanes).  Per variant:
     the force evaluation's device ms per launch (profiled launches, CUDA
     events; with half lists the force kernel and its epilogue kernel), its HBM
     fraction over its own algorithmic bytes, and the whole step's throughput
@@ -312,13 +314,16 @@ def variants_leg(sysd, stream, hbm_peak):
     from paper_2109_09056_b300 import MDSystem
     res = {"workload": "see config",
            "axis": "lanes_per_atom; half: 4 lanes, half lists; aosoaV: 4 lanes, neighbor "
-                   "gathers from an AoSoA shadow copy of vector length V",
+                   "gathers from an AoSoA shadow copy of vector length V; fp64: the FP64 path, "
+                   "automatic lanes; fp64_half: the FP64 path, 4 lanes, half lists",
            "md_steps": 2 * MD_PER_STEP}
-    for lanes in (1, 2, 4, 8, "half", "aosoa8", "aosoa32"):
+    for lanes in (1, 2, 4, 8, "half", "aosoa8", "aosoa32", "fp64", "fp64_half"):
         named = isinstance(lanes, str)
-        m = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="mixed", rc=sysd.rc,
-                     skin=sysd.skin, dt=sysd.dt, rebuild_every=sysd.rebuild_every,
-                     lanes_per_atom=4 if named else lanes, half_list=lanes == "half",
+        fp64 = named and lanes.startswith("fp64")
+        m = MDSystem(sysd.x, sysd.v, sysd.types, sysd.box, precision="fp64" if fp64 else "mixed",
+                     rc=sysd.rc, skin=sysd.skin, dt=sysd.dt, rebuild_every=sysd.rebuild_every,
+                     lanes_per_atom=0 if lanes == "fp64" else (4 if named else lanes),
+                     half_list=lanes in ("half", "fp64_half"),
                      shadow_vl=int(lanes[5:]) if named and lanes.startswith("aosoa") else 0,
                      stream=stream)
         m.step(MD_PER_STEP)

@@ -84,11 +84,12 @@ typedef struct {
                                     (768 when the system has enough warp-tiles and it fits) */
     int32_t use_graphs;          /* 1: md_step replays one rebuild period as a CUDA graph */
     int32_t half_list;           /* 1: half Verlet lists (Newton's third law: each pair once,
-                                    its reaction added to the partner by FP32 atomics); mixed
-                                    precision with 4 lanes per atom only (else MD_ERR_ARG);
-                                    forces are then reproducible to rounding, not bitwise;
-                                    md_force_backward and md_spme_create refuse such a
-                                    context.  0: full lists (default). */
+                                    its reaction added to the partner by atomics, FP32 in a
+                                    mixed context, FP64 in an FP64 one); 4 lanes per atom
+                                    only (else MD_ERR_ARG); forces are then reproducible to
+                                    rounding, not bitwise; md_force_backward and
+                                    md_spme_create refuse such a context.  0: full lists
+                                    (default). */
     int32_t shadow_vl;           /* layout the mixed force kernel gathers neighbor positions
                                     from: 0 = one float4 (x, y, z, type) per atom (default);
                                     8 or 32 = blocks of that many atoms holding x[], y[],

@@ -67,7 +67,7 @@ void free_all(md_ctx *c) {
     F(c->cell); F(c->rank); F(c->perm); F(c->ptmp); F(c->count); F(c->cstart); F(c->nn);
     F(c->nbr); F(c->dbox); F(c->tile_box); F(c->cell_box); F(c->dpair); F(c->dflags);
     F(c->tpart); F(c->tbox); F(c->fpart); F(c->tlog); F(c->dscratch); F(c->stage);
-    F(c->restage); F(c->scan_part); F(c->ctab); F(c->facc); F(c->shv);
+    F(c->restage); F(c->scan_part); F(c->ctab); F(c->facc); F(c->facc64); F(c->shv);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->htbox) cudaFreeHost(c->htbox);
     for (auto &g : c->gexec)
@@ -296,8 +296,8 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     c->T = p.lanes_per_atom ? p.lanes_per_atom : 4;  // automatic: see below for FP64
     if (c->T != 1 && c->T != 2 && c->T != 4 && c->T != 8)
         return fail(c, MD_ERR_ARG, "lanes_per_atom must be 1, 2, 4 or 8");
-    if (p.half_list && (p.precision != MD_MIXED || c->T != 4))
-        return fail(c, MD_ERR_ARG, "half_list needs MD_MIXED and 4 lanes per atom");
+    if (p.half_list && c->T != 4)
+        return fail(c, MD_ERR_ARG, "half_list needs 4 lanes per atom");
     if (p.shadow_vl != 0 && ((p.shadow_vl != 8 && p.shadow_vl != 32) || p.precision != MD_MIXED ||
                              c->T != 4 || p.half_list))
         return fail(c, MD_ERR_ARG, "shadow_vl must be 0, or 8 or 32 with MD_MIXED, 4 lanes, full lists");
@@ -353,7 +353,8 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
     // balance best, once there are atoms enough for many waves of 32-atom warps
     // (B300: 4M atoms 2.98e8 atom-steps/s at 1 lane vs 2.86e8 at 4; 131k atoms
     // 2.44e8 vs 2.71e8, 4,000 atoms 2.6e7 vs 7.8e7).
-    if (!p.lanes_per_atom && p.precision == MD_FP64 && c->n_total >= 8192LL * c->nsm) c->T = 1;
+    if (!p.lanes_per_atom && p.precision == MD_FP64 && !p.half_list && c->n_total >= 8192LL * c->nsm)
+        c->T = 1;
 
     const size_t ns = (size_t)c->ns;
     for (int k = 0; k < 2; ++k) {
@@ -377,9 +378,13 @@ md_status init_ctx(md_ctx *c, int32_t nbox, const int64_t *n_per_box, const md_b
         const size_t blocks = (ns + 1 + p.shadow_vl - 1) / p.shadow_vl;
         CK(dalloc(&c->shv, blocks * 4 * (size_t)p.shadow_vl));
     }
-    if (p.half_list) {  // kept at zero between force evaluations
+    if (p.half_list && p.precision == MD_MIXED) {  // kept at zero between force evaluations
         CK(dalloc(&c->facc, ns + 1));
         CK(cudaMemset(c->facc, 0, (ns + 1) * sizeof(float4)));
+    }
+    if (p.half_list && p.precision == MD_FP64) {
+        CK(dalloc(&c->facc64, 4 * (ns + 1)));
+        CK(cudaMemset(c->facc64, 0, 4 * (ns + 1) * sizeof(double)));
     }
     CK(dalloc(&c->rbuild, 3 * ns));
     CK(dalloc(&c->xw, 3 * ns));

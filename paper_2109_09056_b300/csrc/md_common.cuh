@@ -213,6 +213,7 @@ struct md_ctx {
     double *tlog = nullptr;        // log rows * 4
     int32_t tlog_cap = 0;
     float4 *facc = nullptr;        // half lists: per-slot force + energy accumulators (ns + 1)
+    double *facc64 = nullptr;      // half lists, FP64 context: the same, 4 doubles per slot
     float *shv = nullptr;          // shadow_vl > 0: AoSoA copy of the shadows (slots 0..ns)
     double *dscratch = nullptr;    // adjoint partials etc.
     size_t dscratch_bytes = 0;

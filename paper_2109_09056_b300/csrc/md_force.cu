@@ -61,6 +61,7 @@ struct ForceArgs {
     unsigned int *done;
     uint32_t tx_extra;  // test hook: list-copy bytes that never arrive (0 normally)
     float4 *facc;       // half lists: force (x, y, z) and energy accumulators per slot
+    double *facc64;     // half lists, FP64 context: the same, 4 doubles per slot
     const float *shv;   // shadow_vl > 0: the shadows in blocks of x[VL], y[VL], z[VL], type[VL]
 };
 
@@ -262,7 +263,7 @@ __device__ __forceinline__ void finish_tile(const ForceArgs &a, const SmemTabs &
 // Warp w of the grid takes warp-tiles w, w + nwarps, ...; each lane walks its
 // share of the atom's row (entries sub, sub + T, ...) kBatch entries at a time:
 // the list words, then the neighbor positions, then the pair terms.
-template <int T, bool ONE, bool THERMO>
+template <int T, bool ONE, bool THERMO, bool HALF>
 __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs &tb,
                                              double (*s_offd)[81], float (*s_offf)[81]) {
     constexpr int A = 32 / T;
@@ -301,7 +302,7 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
 #pragma unroll
         for (int k = 0; k < TileState<T>::NC; ++k) {
             const int d = sub + k * T;
-            const bool on = valid && d < 3 && a.mode == MODE_FUSED;
+            const bool on = !HALF && valid && d < 3 && a.mode == MODE_FUSED;
             st.v[k] = on ? __ldcs(a.v + (int64_t)(on ? d : 0) * a.ns + i) : 0.0;
             st.r[k] = d == 0 ? rix : (d == 1 ? riy : riz);
         }
@@ -386,14 +387,36 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                     fx -= phi * dx;
                     fy -= phi * dy;
                     fz -= phi * dz;
-                    if (THERMO) pe += 0.5 * (e4 * s6 * (s6 - 1.0) - ush);
+                    const double up = THERMO ? 0.5 * (e4 * s6 * (s6 - 1.0) - ush) : 0.0;
+                    if (THERMO) pe += up;
+                    if (HALF) {
+                        // the pair is listed once: its reaction (and the other
+                        // half of its energy) goes to the partner's accumulator
+                        double *pj = a.facc64 + 4 * (int64_t)(e[u] & MD_IDX_MASK);
+                        atomicAdd(pj + 0, phi * dx);
+                        atomicAdd(pj + 1, phi * dy);
+                        atomicAdd(pj + 2, phi * dz);
+                        if (THERMO) atomicAdd(pj + 3, up);
+                    }
                 }
             }
           }
         }
         const double Fd[3] = {sum_lanes_d<T>(fx), sum_lanes_d<T>(fy), sum_lanes_d<T>(fz)};
         const double ped = THERMO ? sum_lanes_d<T>(pe) : 0.0;
-        finish_tile<T, THERMO, true>(a, tb, wt, i, valid, ti, Fd, ped, st);
+        if (HALF) {
+            // the atom's own sums join the reactions in its accumulator; the
+            // epilogue kernel integrates
+            if (valid && sub == 0) {
+                double *pi = a.facc64 + 4 * i;
+                atomicAdd(pi + 0, Fd[0]);
+                atomicAdd(pi + 1, Fd[1]);
+                atomicAdd(pi + 2, Fd[2]);
+                if (THERMO) atomicAdd(pi + 3, ped);
+            }
+        } else {
+            finish_tile<T, THERMO, true>(a, tb, wt, i, valid, ti, Fd, ped, st);
+        }
     }
 }
 
@@ -986,10 +1009,10 @@ __global__ void __launch_bounds__(256) k_half_epilogue(ForceArgs a) {
     kernel_done(a, clock, thermo);
 }
 
-template <int T, bool ONE>
+template <int T, bool ONE, bool HALF>
 __global__ void __launch_bounds__(kBlock64, 2) k_force64(ForceArgs a) {
     if (a.fl->status & ST_FREEZE) {
-        mirror_state(a);
+        if (!HALF) mirror_state(a);  // half lists: the epilogue kernel mirrors
         return;
     }
     __shared__ SmemTabs tb;
@@ -999,8 +1022,43 @@ __global__ void __launch_bounds__(kBlock64, 2) k_force64(ForceArgs a) {
     __syncthreads();
     const int64_t clock = a.fl->clock;
     const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
-    if (thermo) force_body64<T, ONE, true>(a, tb, s_offd, s_offf64);
-    else force_body64<T, ONE, false>(a, tb, s_offd, s_offf64);
+    if (thermo) force_body64<T, ONE, true, HALF>(a, tb, s_offd, s_offf64);
+    else force_body64<T, ONE, false, HALF>(a, tb, s_offd, s_offf64);
+    if (!HALF) kernel_done(a, clock, thermo);
+}
+
+// Half lists in an FP64 context, after k_force64<4, ONE, true>: as
+// k_half_epilogue, on the FP64 accumulators (x, y, z, energy per slot).
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_half_epilogue64(ForceArgs a) {
+    if (a.fl->status & ST_FREEZE) {
+        mirror_state(a);
+        return;
+    }
+    __shared__ SmemTabs tb;
+    load_tabs(*a.pair, tb);
+    __syncthreads();
+    const int64_t clock = a.fl->clock;
+    const bool thermo = a.mode != MODE_FUSED || (a.thermo_every > 0 && clock % a.thermo_every == 0);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wt < a.nwt;
+         wt += nw) {
+        const int64_t i = wt * 8 + (lane >> 2);
+        const Box &B = a.boxes[a.tile_box[(wt * 8) >> 5]];
+        const bool valid = (i - B.slot_off) < B.n;
+        double *pi = a.facc64 + 4 * i;
+        const double F[3] = {pi[0], pi[1], pi[2]};
+        const double e = pi[3];
+        __syncwarp();
+        if ((lane & 3) == 0) {
+            pi[0] = 0.0; pi[1] = 0.0; pi[2] = 0.0; pi[3] = 0.0;
+        }
+        const int ti = ONE ? 0 : a.type[i];
+        TileState<4> st;
+        if (thermo) finish_tile<4, true, false>(a, tb, wt, i, valid, ti, F, e, st);
+        else finish_tile<4, false, false>(a, tb, wt, i, valid, ti, F, 0.0, st);
+    }
     kernel_done(a, clock, thermo);
 }
 
@@ -1221,7 +1279,7 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         if (g == 0) {
             int per = 0;
             cudaError_t e =
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force64<T, ONE>, block, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force64<T, ONE, HALF>, block, 0);
             if (e != cudaSuccess) return e;
             g = per > 0 ? per : 1;
             grid_cache[block / 32].store(g, std::memory_order_relaxed);
@@ -1231,7 +1289,12 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
         const int64_t need = (a.nwt + warps_per_block - 1) / warps_per_block;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
-        k_force64<T, ONE><<<(unsigned)grid, block, 0, c->stream>>>(a);
+        k_force64<T, ONE, HALF><<<(unsigned)grid, block, 0, c->stream>>>(a);
+        if constexpr (HALF) {
+            const int64_t blocks = std::min<int64_t>((a.nwt + 7) / 8, (int64_t)c->nsm * 8);
+            k_half_epilogue64<ONE><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+            c->kernels += 1;
+        }
     }
     c->kernels += 1;
     return cudaGetLastError();
@@ -1240,9 +1303,9 @@ cudaError_t launch_force_t(md_ctx *c, const ForceArgs &a) {
 template <bool MIXED>
 cudaError_t launch_force_m(md_ctx *c, const ForceArgs &a) {
     const bool one = c->hpair.nt == 1;
-    if (MIXED && c->params.half_list) {  // 4 lanes per atom (checked at create)
-        return one ? launch_force_t<true, 4, true, true>(c, a)
-                   : launch_force_t<true, 4, false, true>(c, a);
+    if (c->params.half_list) {  // 4 lanes per atom (checked at create)
+        return one ? launch_force_t<MIXED, 4, true, true>(c, a)
+                   : launch_force_t<MIXED, 4, false, true>(c, a);
     }
     if (MIXED && c->params.shadow_vl == 8) {  // 4 lanes per atom (checked at create)
         return one ? launch_force_t<true, 4, true, false, 8>(c, a)
@@ -1291,6 +1354,7 @@ cudaError_t launch_force(md_ctx *c, int mode) {
     a.done = &c->dflags->done;
     a.tx_extra = c->debug_tx_extra;
     a.facc = c->facc;
+    a.facc64 = c->facc64;
     a.shv = c->shv;
     cudaError_t e = c->params.precision == MD_MIXED ? launch_force_m<true>(c, a)
                                                     : launch_force_m<false>(c, a);

@@ -1,16 +1,17 @@
 """Half Verlet lists (md_params.half_list, Newton's third law): each unordered
 pair is listed once, by the atom whose cell is behind the partner's in the
 stencil order (or, in one cell, by the earlier atom), and its reaction is added
-to the partner's accumulator.  Mixed precision, 4 lanes per atom.
+to the partner's accumulator (FP32 atomics in a mixed context, FP64 in an FP64
+one).  4 lanes per atom.
 
 Bars: the half rows hold every pair once, and together with their reversals
 they are exactly the FP64 oracle's full list (integer sets, bit-exact); forces
-within relative L2 1e-5 of the oracle (the mixed bar) and potential energy to
-1e-5 for single boxes (2, 3 and 5 cells per axis, and a compressed box whose
-home cells straddle the build's staging windows); in a batch, forces to 1e-5
-and energies against the full-list run; a 45-step run
-stays within 1e-6 of the full-list run; the calls that need full lists refuse
-a half-list context.
+within relative L2 1e-5 (mixed) / 1e-10 (FP64) of the oracle and potential
+energy to 1e-5 / 1e-10 for single boxes (2, 3 and 5 cells per axis, and a
+compressed box whose home cells straddle the build's staging windows); in a
+batch, forces to 1e-5 and energies against the full-list run; a 45-step run
+stays within 1e-6 (mixed) / 1e-10 (FP64) of the full-list run; the calls that
+need full lists refuse a half-list context.
 """
 import numpy as np
 import pytest
@@ -73,15 +74,37 @@ def test_half_rows_hold_each_pair_once_and_symmetrize_to_the_oracle(name):
 
 
 @pytest.mark.parametrize("name", NAMES)
-def test_half_list_forces_and_energy_match_the_oracle(name):
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_half_list_forces_and_energy_match_the_oracle(name, precision):
     s = boxes()[name]
-    sysm = make(s, "mixed", half_list=True)
+    tol = 1e-5 if precision == "mixed" else 1e-10
+    sysm = make(s, precision, half_list=True)
     pe = sysm.compute_forces()
     f = sysm.state()["f"]
     f_o, _, pe_o = oracle.lj_forces(oracle.wrap(s.x, s.box)[0], s.types, s.box)
-    assert rel_l2(f, f_o) <= 1e-5
-    assert pe == pytest.approx(pe_o, rel=1e-5)
+    assert rel_l2(f, f_o) <= tol
+    assert pe == pytest.approx(pe_o, rel=tol)
     sysm.close()
+
+
+def test_half_list_fp64_after_steps_and_rebuilds_matches_the_full_list_run():
+    """FP64: 45 steps (rebuilds at 20 and 40) with half lists against full
+    lists, positions and total energy to 1e-10, forces on the final positions
+    against the oracle to 1e-10."""
+    s = mi.lj_melt(10, seed=10)
+    half = make(s, "fp64", half_list=True)
+    full = make(s, "fp64")
+    th_h = half.step(45)
+    th_f = full.step(45)
+    sh, sf = half.state(), full.state()
+    f_o, _, _ = oracle.lj_forces(oracle.wrap(sh["x"], s.box)[0], s.types, s.box)
+    assert rel_l2(sh["f"], f_o) <= 1e-10
+    xh = sh["x"] + sh["img"] * s.box
+    xf = sf["x"] + sf["img"] * s.box
+    assert rel_l2(xh, xf) <= 1e-10
+    assert th_h["etot"] == pytest.approx(th_f["etot"], rel=1e-10)
+    half.close()
+    full.close()
 
 
 def test_half_list_after_steps_and_rebuilds_matches_the_oracle():
@@ -132,7 +155,7 @@ def test_half_list_batch_per_box():
 def test_half_list_refusals():
     s = mi.lj_melt(6, seed=3)
     with pytest.raises(MDError):
-        make(s, "fp64", half_list=True)
+        make(s, "fp64", half_list=True, lanes_per_atom=8)
     with pytest.raises(MDError):
         make(s, "mixed", half_list=True, lanes_per_atom=8)
     sysm = make(s, "mixed", half_list=True)
