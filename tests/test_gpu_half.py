@@ -126,30 +126,37 @@ def test_half_list_after_steps_and_rebuilds_matches_the_oracle():
     full.close()
 
 
-def test_half_list_batch_per_box():
-    """Per box: forces against the oracle (1e-5); potential energy against the
-    full-list mixed run of the same batch, to 1e-6 of the summed per-atom
-    energy magnitudes (both share the FP32 pair arithmetic, whose energy error
-    shows most in box 7, a compressed lattice of 286 atoms on 500 sites where
-    pair energies of both signs sum to a small total)."""
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_half_list_batch_per_box(precision):
+    """Per box: forces against the oracle (1e-5 mixed, 1e-10 FP64); potential
+    energy against the full-list run of the same batch, to 1e-6 (mixed) /
+    1e-12 (FP64) of the summed per-atom energy magnitudes (in the mixed path
+    both share the FP32 pair arithmetic, whose energy error shows most in box
+    7, a compressed lattice of 286 atoms on 500 sites where pair energies of
+    both signs sum to a small total); FP64 energies also against the oracle's
+    (1e-10)."""
     ens = mi.ensemble(nbox=8, seed=5, n_lo=256, n_hi=3000)
     x = np.concatenate([b.x for b in ens])
     v = np.concatenate([b.v for b in ens])
     t = np.concatenate([b.types for b in ens])
     th, f = {}, None
     for half in (True, False):
-        sysm = MDSystem(x, v, t, None, precision="mixed", n_per_box=[b.n for b in ens],
-                        boxes=[b.box for b in ens], half_list=half, stream=torch.cuda.Stream())
+        sysm = MDSystem(x, v, t, None, precision=precision, n_per_box=[b.n for b in ens],
+                        boxes=[b.box for b in ens], half_list=half, lanes_per_atom=4,
+                        stream=torch.cuda.Stream())
         sysm.compute_forces()
         if half:
             f = sysm.state()["f"]
         th[half] = sysm.batch_thermo()
         sysm.close()
+    ftol, etol = (1e-5, 1e-6) if precision == "mixed" else (1e-10, 1e-12)
     off = np.concatenate([[0], np.cumsum([b.n for b in ens])])
     for k, b in enumerate(ens):
-        f_o, e_o, _ = oracle.lj_forces(oracle.wrap(b.x, b.box)[0], b.types, b.box)
-        assert rel_l2(f[off[k]:off[k + 1]], f_o) <= 1e-5, k
-        assert abs(th[True][k]["pe"] - th[False][k]["pe"]) <= 1e-6 * np.abs(e_o).sum(), k
+        f_o, e_o, pe_o = oracle.lj_forces(oracle.wrap(b.x, b.box)[0], b.types, b.box)
+        assert rel_l2(f[off[k]:off[k + 1]], f_o) <= ftol, k
+        assert abs(th[True][k]["pe"] - th[False][k]["pe"]) <= etol * np.abs(e_o).sum(), k
+        if precision == "fp64":
+            assert th[True][k]["pe"] == pytest.approx(pe_o, rel=1e-10), k
 
 
 def test_half_list_refusals():
