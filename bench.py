@@ -280,6 +280,31 @@ def spme_leg(args, stream, hbm_peak):
         m.close()
     res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     res["hbm_peak_gbs"] = hbm_peak
+    # half Verlet lists (4 lanes per atom; each pair once, reactions by FP64
+    # atomics): whole calls and the real-space stage, each precision
+    half = {}
+    for prec in ("mixed", "fp64"):
+        m = MDSystem(s.x, s.v, s.types, s.box, precision=prec, half_list=True, stream=stream)
+        sp = SPME(m, cs.q, alpha=cs.alpha, rc=cs.rc, K=K, order=cs.order)
+        dev = torch.device("cuda")
+        for _ in range(3):
+            sp.compute(device=dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sp.compute(device=dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sp.profile(True)
+        sp.compute(device=dev)
+        real_ms = float(sp.profile_read()["real"])
+        sp.profile(False)
+        half[prec] = {"ms_per_call": e0.elapsed_time(e1) / reps, "real_ms": real_ms}
+        sp.close()
+        m.close()
+    res["half_lists"] = half
     if not args.no_cpu:
         # the oracle (numpy FP64: SPME reciprocal part + brute-force real space)
         # on the small charged box, for scale

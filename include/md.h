@@ -87,9 +87,9 @@ typedef struct {
                                     its reaction added to the partner by atomics, FP32 in a
                                     mixed context, FP64 in an FP64 one); 4 lanes per atom
                                     only (else MD_ERR_ARG); forces are then reproducible to
-                                    rounding, not bitwise; md_force_backward and
-                                    md_spme_create refuse such a context.  0: full lists
-                                    (default). */
+                                    rounding, not bitwise; md_force_backward refuses such a
+                                    context (the SPME solver's real-space pass takes half
+                                    lists too).  0: full lists (default). */
     int32_t shadow_vl;           /* layout the mixed force kernel gathers neighbor positions
                                     from: 0 = one float4 (x, y, z, type) per atom (default);
                                     8 or 32 = blocks of that many atoms holding x[], y[],

@@ -576,7 +576,12 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
 // With LJ, the same walk of the list also takes the LJ 12-6 pair terms of the
 // context (its cutoff, which is at least rc, its eps/sigma tables and shift)
 // and writes F_LJ + F_real: the force pass of a Coulomb + LJ step.
-template <int T, bool MIXED, bool LJ>
+//
+// Half lists (HALF): each pair is listed once; fs starts at zero, the atom's
+// own sums and each pair's reaction (FP64 atomics) are added into it, and the
+// energy partials count each pair once (doubled below to the full-list
+// convention of two halves per pair).
+template <int T, bool MIXED, bool LJ, bool HALF>
 __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
     constexpr int A = 32 / T;
     __shared__ double s_offd[81];
@@ -682,6 +687,12 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                             bx = fmaf(-g, dx, bx);
                             by = fmaf(-g, dy, by);
                             bz = fmaf(-g, dz, bz);
+                            if (HALF) {
+                                const int64_t j = e[u] & MD_IDX_MASK;
+                                atomicAdd(a.fs + j, (double)(g * dx));
+                                atomicAdd(a.fs + a.ns + j, (double)(g * dy));
+                                atomicAdd(a.fs + 2 * a.ns + j, (double)(g * dz));
+                            }
                         }
                     } else if (qj[u] != 0.f && r2 < a.rc2f) {
                         const float qq = qi * qj[u];
@@ -693,6 +704,12 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                         by = fmaf(-g, dy, by);
                         bz = fmaf(-g, dz, bz);
                         be = fmaf(0.5f * qq, er * rinv, be);
+                        if (HALF) {
+                            const int64_t j = e[u] & MD_IDX_MASK;
+                            atomicAdd(a.fs + j, (double)(g * dx));
+                            atomicAdd(a.fs + a.ns + j, (double)(g * dy));
+                            atomicAdd(a.fs + 2 * a.ns + j, (double)(g * dz));
+                        }
                     }
                 }
                 kahan_add(fx, cx, bx);
@@ -761,6 +778,11 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 fx -= g * dx;
                 fy -= g * dy;
                 fz -= g * dz;
+                if (HALF && g != 0.0) {
+                    atomicAdd(a.fs + j, g * dx);
+                    atomicAdd(a.fs + a.ns + j, g * dy);
+                    atomicAdd(a.fs + 2 * a.ns + j, g * dz);
+                }
               }
             }
             F[0] = fx;
@@ -776,8 +798,15 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
         }
         if (valid && sub == 0) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) a.fs[d * a.ns + i] = F[d];
+            for (int d = 0; d < 3; ++d) {
+                if (HALF) atomicAdd(a.fs + d * a.ns + i, F[d]);
+                else a.fs[d * a.ns + i] = F[d];
+            }
         }
+    }
+    if (HALF) {
+        pe_lane *= 2.0;
+        pl_lane *= 2.0;
     }
     cta_sum_to<kRealBlock>(pe_lane, a.part + blockIdx.x);
     if (LJ) {
@@ -944,14 +973,16 @@ md_status check_erfc_on_device(md_spme *s) {
     return MD_OK;
 }
 
-template <int T, bool MIXED, bool LJ>
+template <int T, bool MIXED, bool LJ, bool HALF = false>
 cudaError_t launch_real_t(const RealArgs &ra, int blocks, cudaStream_t st) {
-    k_spme_real<T, MIXED, LJ><<<blocks, kRealBlock, 0, st>>>(ra);
+    k_spme_real<T, MIXED, LJ, HALF><<<blocks, kRealBlock, 0, st>>>(ra);
     return cudaGetLastError();
 }
 
+// half lists: 4 lanes per atom (checked when the context is created)
 template <bool MIXED, bool LJ>
-cudaError_t launch_real_l(int T, const RealArgs &ra, int blocks, cudaStream_t st) {
+cudaError_t launch_real_l(int T, bool half, const RealArgs &ra, int blocks, cudaStream_t st) {
+    if (half) return T == 4 ? launch_real_t<4, MIXED, LJ, true>(ra, blocks, st) : cudaErrorInvalidValue;
     switch (T) {
         case 1: return launch_real_t<1, MIXED, LJ>(ra, blocks, st);
         case 2: return launch_real_t<2, MIXED, LJ>(ra, blocks, st);
@@ -962,13 +993,13 @@ cudaError_t launch_real_l(int T, const RealArgs &ra, int blocks, cudaStream_t st
 }
 
 // Resident CTAs per SM of a real-space kernel variant (occupancy API, cached).
-template <int T, bool MIXED, bool LJ>
+template <int T, bool MIXED, bool LJ, bool HALF = false>
 int real_residency() {
     static std::atomic<int> cached{0};
     int v = cached.load();
     if (v == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spme_real<T, MIXED, LJ>, kRealBlock,
-                                                          0) != cudaSuccess || v < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spme_real<T, MIXED, LJ, HALF>,
+                                                          kRealBlock, 0) != cudaSuccess || v < 1) {
             cudaGetLastError();
             v = 1;
         }
@@ -978,7 +1009,8 @@ int real_residency() {
 }
 
 template <bool MIXED, bool LJ>
-int real_residency_l(int T) {
+int real_residency_l(int T, bool half) {
+    if (half) return real_residency<4, MIXED, LJ, true>();
     switch (T) {
         case 1: return real_residency<1, MIXED, LJ>();
         case 2: return real_residency<2, MIXED, LJ>();
@@ -987,17 +1019,17 @@ int real_residency_l(int T) {
     }
 }
 
-int real_residency_any(bool mixed, bool lj, int T) {
-    if (mixed) return lj ? real_residency_l<true, true>(T) : real_residency_l<true, false>(T);
-    return lj ? real_residency_l<false, true>(T) : real_residency_l<false, false>(T);
+int real_residency_any(bool mixed, bool lj, int T, bool half) {
+    if (mixed) return lj ? real_residency_l<true, true>(T, half) : real_residency_l<true, false>(T, half);
+    return lj ? real_residency_l<false, true>(T, half) : real_residency_l<false, false>(T, half);
 }
 
-cudaError_t launch_real(bool mixed, bool lj, int T, const RealArgs &ra, int blocks,
+cudaError_t launch_real(bool mixed, bool lj, int T, bool half, const RealArgs &ra, int blocks,
                         cudaStream_t st) {
-    if (mixed) return lj ? launch_real_l<true, true>(T, ra, blocks, st)
-                         : launch_real_l<true, false>(T, ra, blocks, st);
-    return lj ? launch_real_l<false, true>(T, ra, blocks, st)
-              : launch_real_l<false, false>(T, ra, blocks, st);
+    if (mixed) return lj ? launch_real_l<true, true>(T, half, ra, blocks, st)
+                         : launch_real_l<true, false>(T, half, ra, blocks, st);
+    return lj ? launch_real_l<false, true>(T, half, ra, blocks, st)
+              : launch_real_l<false, false>(T, half, ra, blocks, st);
 }
 
 template <int P, typename R>
@@ -1171,7 +1203,6 @@ md_status md_spme_create(md_ctx *c, const double *q, const md_spme_params *p, md
     *out = nullptr;
     if (!c || !q || !p) return sfail(nullptr, MD_ERR_ARG, "NULL argument");
     if (c->nbox != 1) return sfail(nullptr, MD_ERR_ARG, "SPME needs a single-box context");
-    if (c->params.half_list) return sfail(nullptr, MD_ERR_ARG, "SPME needs full lists");
     if (!(p->alpha > 0.0) || !std::isfinite(p->alpha))
         return sfail(nullptr, MD_ERR_ARG, "alpha must be positive and finite");
     if (!(p->rc > 0.0) || !(p->rc <= c->params.rc))
@@ -1270,8 +1301,9 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     // its call) and a profiled pass take one warp per tile
     const bool overlap = !s->prof;
     const int64_t tiles_blocks = (ra.nwt + kRealBlock / 32 - 1) / (kRealBlock / 32);
+    const bool half = c->params.half_list != 0;
     const int per_sm =
-        std::min(lj ? kFusedCtasPerSm : kRealCtasPerSm, real_residency_any(mixed, lj, c->T));
+        std::min(lj ? kFusedCtasPerSm : kRealCtasPerSm, real_residency_any(mixed, lj, c->T, half));
     const int real_blocks = (int)std::min<int64_t>(
         tiles_blocks, overlap && mixed ? (int64_t)per_sm * c->nsm : tiles_blocks);
     if (real_blocks > s->nreal) return sfail(s, MD_ERR_ARG, "internal: real-space partials");
@@ -1283,7 +1315,8 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     if (overlap) {
         SCK(cudaEventRecord(s->fork, stream));
         SCK(cudaStreamWaitEvent(s->side, s->fork, 0));
-        SCK(launch_real(mixed, lj, c->T, ra, real_blocks, s->side));
+        if (half) SCK(cudaMemsetAsync(ra.fs, 0, 3 * (size_t)c->ns * sizeof(double), s->side));
+        SCK(launch_real(mixed, lj, c->T, half, ra, real_blocks, s->side));
         SCK(cudaEventRecord(s->join, s->side));
     }
     const size_t rb = s->f32 ? sizeof(float) : sizeof(double);
@@ -1292,7 +1325,10 @@ md_status enqueue(md_spme *s, double *out, bool acc, bool lj) {
     SCK(launch_atoms_any(s->f32, s->p.order, kSpread, aa, s->qs, s->grid, nullptr, nullptr,
                          stream));
     SCK(mark(1));
-    if (!overlap) SCK(launch_real(mixed, lj, c->T, ra, real_blocks, stream));
+    if (!overlap) {
+        if (half) SCK(cudaMemsetAsync(ra.fs, 0, 3 * (size_t)c->ns * sizeof(double), stream));
+        SCK(launch_real(mixed, lj, c->T, half, ra, real_blocks, stream));
+    }
     SCK(mark(2));
     SCK(fft3_forward_xy(s->fft, s->grid, s->ghat, stream));
     SCK(mark(3));

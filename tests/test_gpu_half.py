@@ -10,8 +10,9 @@ within relative L2 1e-5 (mixed) / 1e-10 (FP64) of the oracle and potential
 energy to 1e-5 / 1e-10 for single boxes (2, 3 and 5 cells per axis, and a
 compressed box whose home cells straddle the build's staging windows); in a
 batch, forces to 1e-5 and energies against the full-list run; a 45-step run
-stays within 1e-6 (mixed) / 1e-10 (FP64) of the full-list run; the calls that
-need full lists refuse a half-list context.
+stays within 1e-6 (mixed) / 1e-10 (FP64) of the full-list run; the adjoint,
+which needs full lists, refuses a half-list context (the SPME solver takes
+half lists: tests/test_gpu_spme*.py).
 """
 import numpy as np
 import pytest
@@ -26,7 +27,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 from gpu_util import RS, make, rel_l2  # noqa: E402
-from paper_2109_09056_b300 import SPME, MDError, MDSystem  # noqa: E402
+from paper_2109_09056_b300 import MDError, MDSystem  # noqa: E402
 
 
 def boxes():
@@ -168,7 +169,4 @@ def test_half_list_refusals():
     sysm = make(s, "mixed", half_list=True)
     with pytest.raises(MDError):
         sysm.force_backward(np.zeros((s.n, 3)))
-    with pytest.raises(MDError):
-        SPME(sysm, mi.neutral_charges(s.n, np.random.default_rng(1)), alpha=1.25, rc=2.5,
-             K=(24, 24, 24))
     sysm.close()

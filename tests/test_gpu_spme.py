@@ -7,7 +7,7 @@ at the same grid and order, and its brute-force real-space erfc sum, to 1e-10
 FP32 real-space pairs with Kahan sums; FP64 energy totals) must match to 1e-5.
 Cases: the three spline orders, ragged non-power-of-two grids, an orthorhombic box, positions after steps (drift and a re-sort), a charged box
 (background term), degenerate charge sets, host and device output buffers, the
-argument checks, and sampled atoms of the 4M-atom workload.
+argument checks, half Verlet lists, and sampled atoms of the 4M-atom workload.
 """
 import numpy as np
 import pytest
@@ -206,6 +206,22 @@ def test_spme_lanes_per_atom(precision, lanes):
     cs = mi.charged_workload("coulomb_fcc10_4000")
     s = cs.lj
     sysm = make(s, precision, lanes_per_atom=lanes)
+    sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, precision)
+    sysm.step(21)                          # a rebuild in between
+    check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, precision)
+    sp.close()
+    sysm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_half_lists(precision):
+    """Half Verlet lists (each pair once, its reaction added to the partner):
+    the real-space pass gives the oracle's energies and forces, before and
+    after a rebuild."""
+    cs = mi.charged_workload("coulomb_fcc10_4000")
+    s = cs.lj
+    sysm = make(s, precision, half_list=True)
     sp = SPME(sysm, cs.q, alpha=cs.alpha, rc=cs.rc, K=cs.K, order=cs.order)
     check_against_oracle(sysm, sp, cs.q, s.box, cs.alpha, cs.rc, cs.K, cs.order, precision)
     sysm.step(21)                          # a rebuild in between

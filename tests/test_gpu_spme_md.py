@@ -257,3 +257,21 @@ def test_spme_step_lanes_per_atom(reference8, precision, lanes):
     assert abs(e["coulomb"] - ec_o) <= tol * abs(ec_o)
     sp.close()
     sysm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_step_half_lists(reference8, precision):
+    """The fused LJ + Coulomb pass on half Verlet lists (reactions added to the
+    partner): 8 steps against the oracle loop."""
+    s, q, (x_o, v_o, pe_o, ec_o, ke_o) = reference8
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    sysm = make(s, precision, half_list=True)
+    sp = SPME(sysm, q, alpha=ALPHA, rc=RC, K=K, order=ORDER)
+    e = sp.step(8)
+    st = sysm.state(forces=False)
+    assert np.linalg.norm(periodic_diff(st["x"], x_o, s.box)) <= tol * np.linalg.norm(x_o)
+    assert rel_l2(st["v"], v_o) <= tol
+    assert abs(e["pe_lj"] - pe_o) <= tol * abs(pe_o)
+    assert abs(e["coulomb"] - ec_o) <= tol * abs(ec_o)
+    sp.close()
+    sysm.close()
