@@ -354,11 +354,13 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                 }
             }
             double xj[kBatch], yj[kBatch], zj[kBatch];
+            int64_t jj[kBatch];  // checked slot indices (half lists: the reactions' targets)
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const bool ok = e[u] != kNoEntry;
                 const int64_t j =
                     ok ? chk_index(e[u] & MD_IDX_MASK, a.ns, CHK_FORCE64_GATHER, a.fl, 0) : 0;
+                jj[u] = j;
                 xj[u] = ok ? __ldg(a.r_in + j) : 1e4;
                 yj[u] = ok ? __ldg(a.r_in + a.ns + j) : 1e4;
                 zj[u] = ok ? __ldg(a.r_in + 2 * a.ns + j) : 1e4;
@@ -392,7 +394,7 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                     if (HALF) {
                         // the pair is listed once: its reaction (and the other
                         // half of its energy) goes to the partner's accumulator
-                        double *pj = a.facc64 + 4 * (int64_t)(e[u] & MD_IDX_MASK);
+                        double *pj = a.facc64 + 4 * jj[u];
                         atomicAdd(pj + 0, phi * dx);
                         atomicAdd(pj + 1, phi * dy);
                         atomicAdd(pj + 2, phi * dz);
@@ -570,7 +572,9 @@ __device__ __forceinline__ void lane_rows(const ForceArgs &a, const SmemTabs &tb
         ty = -phi * dy;
         tz = -phi * dz;
         tp = (THERMO && in) ? 0.5f * fmaf(e4 * s6, s6 - 1.0f, -ush) : 0.0f;
-        if (HALF && in) red_add4(a.facc + (en & MD_IDX_MASK), -tx, -ty, -tz, tp);
+        if (HALF && in)
+            red_add4(a.facc + chk_index(en & MD_IDX_MASK, a.ns + 1, CHK_FORCE_GATHER, a.fl, a.ns),
+                     -tx, -ty, -tz, tp);
     };
     // groups of G consecutive terms are added by an FMA chain, each group
     // sum into the lane's partial by one Kahan step

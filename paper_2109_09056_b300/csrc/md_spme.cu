@@ -649,10 +649,12 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 float4 sj[kRealBatch];
                 float qj[kRealBatch];
                 int tj[kRealBatch];
+                int64_t jj[kRealBatch];  // checked slot indices (half lists: the reactions' targets)
 #pragma unroll
                 for (int u = 0; u < kRealBatch; ++u) {
                     const int64_t j =
                         chk_index(e[u] & MD_IDX_MASK, a.ns + 1, CHK_SPME_GATHER, a.fl, a.ns);
+                    jj[u] = j;
                     sj[u] = __ldg(a.shq + j);
                     qj[u] = sj[u].w;
                     tj[u] = LJ && nt > 1 ? __ldg(a.type + j) : 0;
@@ -687,8 +689,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                             bx = fmaf(-g, dx, bx);
                             by = fmaf(-g, dy, by);
                             bz = fmaf(-g, dz, bz);
-                            if (HALF) {
-                                const int64_t j = e[u] & MD_IDX_MASK;
+                            if (HALF && jj[u] < a.ns) {  // (slot ns: the far dummy)
+                                const int64_t j = jj[u];
                                 atomicAdd(a.fs + j, (double)(g * dx));
                                 atomicAdd(a.fs + a.ns + j, (double)(g * dy));
                                 atomicAdd(a.fs + 2 * a.ns + j, (double)(g * dz));
@@ -704,8 +706,8 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                         by = fmaf(-g, dy, by);
                         bz = fmaf(-g, dz, bz);
                         be = fmaf(0.5f * qq, er * rinv, be);
-                        if (HALF) {
-                            const int64_t j = e[u] & MD_IDX_MASK;
+                        if (HALF && jj[u] < a.ns) {  // (slot ns: the far dummy)
+                            const int64_t j = jj[u];
                             atomicAdd(a.fs + j, (double)(g * dx));
                             atomicAdd(a.fs + a.ns + j, (double)(g * dy));
                             atomicAdd(a.fs + 2 * a.ns + j, (double)(g * dz));
