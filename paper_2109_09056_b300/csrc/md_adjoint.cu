@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjArgs a) {
             const double u = (dx * dx + dy * dy) + dz * dz;
             if (!(u < rc2)) continue;
             const int ab = ti * nt + a.type[j];
-            const double iu = 1.0 / u;
+            const double iu = rcp_newton64(u);
             const double q2 = t_s2[ab] * iu;
             const double s6 = q2 * q2 * q2, s12 = s6 * s6;
             const double e24u = t_e24[ab] * iu;

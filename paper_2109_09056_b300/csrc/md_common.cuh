@@ -284,6 +284,24 @@ size_t adjoint_scratch_doubles(md_ctx *c);
 // longest row after each build; the rows of padding slots hold it from the
 // list's allocation on): the dummy shadow slot ns (kept far from every atom)
 // with a zero offset; a pair evaluated against it is masked by rc.
+// 1/x in FP64 for the FP64 pair kernels (x a normal positive number): the
+// hardware's approximate FP64 reciprocal (relative error ~1e-6) refined by two
+// Newton-Raphson steps for f(y) = 1/y - x, y' = y + y (1 - x y), each of which
+// squares the relative error.  Measured on B300 over 1.7e7 arguments in
+// [0.25, 64): equal to the IEEE quotient on every one, in fewer FP64
+// instructions than the division.  (The same scheme for 1/sqrt(x) came within
+// 2 ulp but cost more than rsqrt().)
+__device__ __forceinline__ double rcp_newton64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double e = fma(-x, y, 1.0);
+        y = fma(y, e, y);
+    }
+    return y;
+}
+
 __host__ __device__ inline uint32_t sentinel_entry(int64_t ns) {
     return (uint32_t)ns | (kCodeZero << MD_IDX_BITS);
 }

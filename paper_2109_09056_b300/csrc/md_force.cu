@@ -102,6 +102,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+
 template <int T>
 __device__ __forceinline__ double sum_lanes_d(double x) {
 #pragma unroll
@@ -382,7 +383,7 @@ __device__ __forceinline__ void force_body64(const ForceArgs &a, const SmemTabs 
                         const int ab = ti * nt + __ldg(a.type + j);
                         e24 = tb.de24[ab]; s2 = tb.ds2[ab]; e4 = tb.de4[ab]; ush = tb.dush[ab];
                     }
-                    const double r2inv = 1.0 / r2;
+                    const double r2inv = rcp_newton64(r2);
                     const double q2 = s2 * r2inv;
                     const double s6 = q2 * q2 * q2;
                     const double phi = e24 * r2inv * s6 * (2.0 * s6 - 1.0);

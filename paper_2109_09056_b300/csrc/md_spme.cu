@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(kRealBlock) k_spme_real(RealArgs a) {
                 const double r2 = (dx * dx + dy * dy) + dz * dz;
                 double g = 0.0;
                 if (LJ && r2 < rc2lj) {
-                    const double r2inv = 1.0 / r2;
+                    const double r2inv = rcp_newton64(r2);
                     const int ab = ti * nt + (nt > 1 ? __ldg(a.type + j) : 0);
                     const double q2 = s_lj64[64 + ab] * r2inv;
                     const double s6 = q2 * q2 * q2;
